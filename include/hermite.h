@@ -1,0 +1,163 @@
+/*
+ * hermite.h -- C ABI of the B300 (sm_103a) Hermite wave-equation library.
+ *
+ * The library advances u_tt = c^2 Lap u with the arbitrary-order Hermite
+ * methods of Appelo, Hagstrom and Vargas, "Hermite Methods for the Scalar
+ * Wave Equation": the dissipative method (Sec. 3; order 2m-1, the "full"
+ * variant of Sec. 3.3 for d > 1) and the conservative method (Sec. 4;
+ * order 2m), on the staggered primal/dual grids of Sec. 2.1 with periodic,
+ * homogeneous Dirichlet or homogeneous Neumann boundaries (Sec. 3.1.3).
+ *
+ * Conventions shared by every entry point
+ *   Domain       [0, N h]^d, N cells per axis.  Periodic: N primal nodes
+ *                (x = i h) and N dual nodes (x = (j+1/2) h) per axis.
+ *                Dirichlet/Neumann: N+1 primal and N dual nodes per axis.
+ *   Host layout  row-major state[node][coef], FP64.  Nodes in C order over
+ *                the axes (axis 0 slowest).  Coefficients: multi-index
+ *                k = (k_0..k_{d-1}) in C order; u has k in [0,m]^d
+ *                (Nu = (m+1)^d values), v has k in [0,m-1]^d (Nv = m^d).
+ *                Values are the paper's scaled derivatives h^|k|/k! d^k u
+ *                and h^|k|/k! d^k v (Sec. 2.2, Sec. 3.1.1).
+ *   Steps        hermite_step(n) performs n full steps = 2n half-steps of
+ *                dt/2 each (Sec. 2.1: primal at t_n, dual at t_{n+1/2}).
+ *   Ownership    The library owns all device memory of a context; the caller
+ *                owns every buffer it passes.  Host pointers are read/written
+ *                synchronously; device pointers are used on the context's
+ *                stream.  No C++ exception crosses this interface.
+ *   Errors       Every int-returning call returns HERMITE_OK (0) or a
+ *                negative HERMITE_ERR_* code; hermite_last_error() gives a
+ *                message for the context.  A failed call leaves the stored
+ *                state unchanged unless the code is HERMITE_ERR_CUDA.
+ *   Threads      A context must not be used by two host threads at once.
+ */
+#ifndef HERMITE_H
+#define HERMITE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hermite_ctx hermite_ctx;
+
+/* Variants: Sec. 3.3 "full" dissipative (special interpolants I_{m,..,m-1}
+ * for the first time derivative; identical to the 1-D method when d = 1),
+ * Sec. 4 conservative, Sec. 3.3 plain tensor-product ("simple") dissipative. */
+enum { HERMITE_DISSIPATIVE = 0, HERMITE_CONSERVATIVE = 1, HERMITE_DISSIPATIVE_SIMPLE = 2 };
+/* Boundaries (Sec. 3.1.3): ghost polynomials are odd (Dirichlet) or even
+ * (Neumann) reflections of the first interior dual node. */
+enum { HERMITE_PERIODIC = 0, HERMITE_DIRICHLET = 1, HERMITE_NEUMANN = 2 };
+/* Grids. */
+enum { HERMITE_PRIMAL = 0, HERMITE_DUAL = 1 };
+
+enum {
+  HERMITE_OK = 0,
+  HERMITE_ERR_ARG = -1,         /* invalid argument (sizes, CFL, pointers) */
+  HERMITE_ERR_ALLOC = -2,       /* device or host allocation failed */
+  HERMITE_ERR_CUDA = -3,        /* a CUDA call failed; see hermite_last_error */
+  HERMITE_ERR_NONFINITE = -4,   /* NaN/Inf found in an energy reduction */
+  HERMITE_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+  HERMITE_ERR_STATE = -6,       /* call not valid in the current state */
+  HERMITE_ERR_UNSUPPORTED = -7  /* (d, m) outside the compiled range */
+};
+
+/* Create a problem (Sec. 2.1 grids; Sec. 3/4 methods).
+ *   d in {1,2,3}; m >= 1 (dissipative) or m >= 0 (conservative); N >= 1
+ *   cells per axis; c > 0 wave speed; h > 0 cell width; dt > 0 with
+ *   0 < c dt / h <= 1 (the CFL bound under which the evolution of the cell
+ *   polynomial at the new node is exact, Sec. 3.1.2 / 4.1).
+ *   Supported (d, m): every m with 2m+1 <= 255 coefficients per node for
+ *   d = 1, m <= 6 for d = 2, m <= 3 for d = 3 (else HERMITE_ERR_UNSUPPORTED).
+ * Allocates both grids on the current CUDA device and builds the per-cell
+ * operator (the interpolation + Taylor evolution + evaluation map of one
+ * cell, Eqs. Hermcon, recursion_diss_1d_1/2, recursion_ut/vt, update) in
+ * FP64 on the device.  The state is zero until set.  *out receives the
+ * context (NULL on error). */
+int hermite_create(int d, int m, int64_t N, double c, double h, double dt,
+                   int variant, int bc, hermite_ctx **out);
+
+/* Release all device memory of the context (NULL is ignored). */
+void hermite_destroy(hermite_ctx *ctx);
+
+/* Run subsequent device work of this context on the given cudaStream_t
+ * (NULL = the legacy default stream). */
+int hermite_set_stream(hermite_ctx *ctx, void *stream);
+
+/* Initial data at t = 0 on the primal grid (Sec. 3.1.1), host buffers:
+ *   u [nodes_primal][Nu], v [nodes_primal][Nv] (v may be NULL = zero).
+ * Dissipative: both levels are the given data.  Conservative (Sec. 4): u is
+ * the primal level at t = 0 and the dual level at t = dt/2 is generated by
+ * the Taylor series of the cell interpolants of (u, v) (the paper leaves the
+ * start-up open); v is ignored when m = 0.  Resets the step counter. */
+int hermite_set_state(hermite_ctx *ctx, const double *u, const double *v);
+
+/* Same with device pointers (same layout), read on the context's stream. */
+int hermite_set_state_device(hermite_ctx *ctx, const double *u, const double *v);
+
+/* Conservative only: both levels given, host buffers, u_primal at t = 0
+ * [nodes_primal][Nu] and u_dual at t = dt/2 [nodes_dual][Nu]. */
+int hermite_set_state2(hermite_ctx *ctx, const double *u_primal, const double *u_dual);
+
+/* Advance n >= 0 full steps (2n half-steps), device work only, enqueued on
+ * the context's stream (asynchronous with respect to the host). */
+int hermite_step(hermite_ctx *ctx, int64_t nsteps);
+
+/* Advance n >= 0 half-steps.  Dissipative: alternately primal->dual and
+ * dual->primal.  Conservative: alternately update the primal level from the
+ * dual one and the dual level from the primal one (Eq. update). */
+int hermite_advance_half(hermite_ctx *ctx, int64_t nhalf);
+
+/* Number of half-steps taken since the state was set. */
+int64_t hermite_half_steps(const hermite_ctx *ctx);
+
+/* Time of the primal level: (half-steps / 2) * dt rounded down to whole steps
+ * for the conservative method, half-steps * dt/2 for the dissipative one. */
+double hermite_time(const hermite_ctx *ctx);
+
+/* Primal-grid state, host buffers [nodes_primal][Nu] / [nodes_primal][Nv]
+ * (v may be NULL; ignored for the conservative method).  Dissipative: valid
+ * after an even number of half-steps (HERMITE_ERR_STATE otherwise).
+ * Synchronises the context's stream. */
+int hermite_get_state(hermite_ctx *ctx, double *u, double *v);
+
+/* Either grid's stored data, host buffers (v may be NULL). */
+int hermite_get_grid(hermite_ctx *ctx, int grid, double *u, double *v);
+/* Overwrite either grid's stored data from host buffers (v may be NULL = 0). */
+int hermite_set_grid(hermite_ctx *ctx, int grid, const double *u, const double *v);
+/* Copy either grid into caller-owned device buffers (same layout). */
+int hermite_get_grid_device(hermite_ctx *ctx, int grid, double *u, double *v);
+
+/* Energies of the latest level (Sec. 3.2, 3.3, 4.2), exact per-cell
+ * quadrature of the piecewise interpolants, FP64 device reduction:
+ *   dissipative  out[0] = int v^2 + c^2 |grad u|^2 over the domain
+ *                out[1] = c^2 sum_i |d_i I^(i) u|^2_{m,..,m} + |I_{m-1} v|^2_{m,..,m}
+ *                         (Eq. stable1 for d = 1, the left side of Eq. stable2
+ *                         for d > 1; non-increasing for d = 1)
+ *   conservative out[0] = c^2 int |grad p^n|^2 of the primal level
+ *                out[1] = G = |p^{n+1/2}|^2_{m+1,..} - <p^{n+1}, p^n>_{m+1,..},
+ *                         conserved by the scheme (equals half the paper's
+ *                         |P+|^2 + |P-|^2 of Eq. Vdef in 1-D)
+ *   out[2] = 0 (reserved).
+ * For non-periodic problems cells cut by the boundary count half per axis.
+ * Returns HERMITE_ERR_NONFINITE if a result is NaN/Inf.  Synchronises. */
+int hermite_energy(hermite_ctx *ctx, double out[3]);
+
+/* Sizes: nodes on a grid, and coefficients per node. */
+int64_t hermite_nodes(const hermite_ctx *ctx, int grid);
+int hermite_ncoef(const hermite_ctx *ctx, int *nu, int *nv);
+
+/* Copy the FP64 per-cell operator of the reference corner (all axes at
+ * xi = -1/2): rows = outputs (u then (h/c) v, or u only), columns = inputs
+ * (u then (h/c) v).  which = 0: half-step operator; 1: conservative start-up
+ * operator.  rows/cols receive the sizes; out may be NULL to query them. */
+int hermite_operator(hermite_ctx *ctx, int which, double *out, int *rows, int *cols);
+
+/* Message of the last failed call on this context ("" if none).  With a NULL
+ * context: the message of the last failed hermite_create in this thread. */
+const char *hermite_last_error(const hermite_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HERMITE_H */

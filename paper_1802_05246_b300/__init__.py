@@ -1,0 +1,197 @@
+"""Python binding of the B300 Hermite wave-equation library (libhermite_b300.so).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  The names mirror the C ABI in ``include/hermite.h``.  Importing
+this package does not need a GPU; creating a context does.  If the shared
+library is missing the import of :func:`lib` raises -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhermite_b300.so")
+
+DISSIPATIVE, CONSERVATIVE, DISSIPATIVE_SIMPLE = 0, 1, 2
+PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
+PRIMAL, DUAL = 0, 1
+
+ERRORS = {
+    -1: "HERMITE_ERR_ARG", -2: "HERMITE_ERR_ALLOC", -3: "HERMITE_ERR_CUDA", -4: "HERMITE_ERR_NONFINITE",
+    -5: "HERMITE_ERR_TIMEOUT", -6: "HERMITE_ERR_STATE", -7: "HERMITE_ERR_UNSUPPORTED",
+}
+
+# every symbol declared in include/hermite.h
+EXPORTS = [
+    "hermite_create", "hermite_destroy", "hermite_set_stream", "hermite_set_state", "hermite_set_state_device",
+    "hermite_set_state2", "hermite_step", "hermite_advance_half", "hermite_half_steps", "hermite_time",
+    "hermite_get_state", "hermite_get_grid", "hermite_set_grid", "hermite_get_grid_device", "hermite_energy",
+    "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error",
+]
+
+
+class HermiteError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} not found: build it with `python -m paper_1802_05246_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, i64, c_int, c_dbl = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "hermite_create": (c_int, [c_int, c_int, i64, c_dbl, c_dbl, c_dbl, c_int, c_int, ctypes.POINTER(vp)]),
+        "hermite_destroy": (None, [vp]),
+        "hermite_set_stream": (c_int, [vp, vp]),
+        "hermite_set_state": (c_int, [vp, vp, vp]),
+        "hermite_set_state_device": (c_int, [vp, vp, vp]),
+        "hermite_set_state2": (c_int, [vp, vp, vp]),
+        "hermite_step": (c_int, [vp, i64]),
+        "hermite_advance_half": (c_int, [vp, i64]),
+        "hermite_half_steps": (i64, [vp]),
+        "hermite_time": (c_dbl, [vp]),
+        "hermite_get_state": (c_int, [vp, vp, vp]),
+        "hermite_get_grid": (c_int, [vp, c_int, vp, vp]),
+        "hermite_set_grid": (c_int, [vp, c_int, vp, vp]),
+        "hermite_get_grid_device": (c_int, [vp, c_int, vp, vp]),
+        "hermite_energy": (c_int, [vp, dp]),
+        "hermite_nodes": (i64, [vp, c_int]),
+        "hermite_ncoef": (c_int, [vp, ip, ip]),
+        "hermite_operator": (c_int, [vp, c_int, vp, ip, ip]),
+        "hermite_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Data pointer of a C-contiguous float64 numpy array or torch tensor (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous float64 array")
+        return a.ctypes.data
+    # torch tensor (host or device)
+    if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+        raise ValueError("expected a contiguous float64 tensor")
+    return a.data_ptr()
+
+
+class Hermite:
+    """One problem on the current CUDA device (see ``hermite_create``)."""
+
+    def __init__(self, d, m, N, c, h, dt, variant=DISSIPATIVE, bc=PERIODIC):
+        L = lib()
+        h_ = ctypes.c_void_p()
+        rc = L.hermite_create(int(d), int(m), int(N), float(c), float(h), float(dt), int(variant), int(bc),
+                              ctypes.byref(h_))
+        if rc != 0:
+            raise HermiteError(rc, L.hermite_last_error(None).decode())
+        self._h = h_
+        self.d, self.m, self.N, self.c, self.h, self.dt = int(d), int(m), int(N), float(c), float(h), float(dt)
+        self.variant, self.bc = int(variant), int(bc)
+        nu, nv = ctypes.c_int(), ctypes.c_int()
+        L.hermite_ncoef(self._h, ctypes.byref(nu), ctypes.byref(nv))
+        self.Nu, self.Nv = nu.value, nv.value
+
+    def _check(self, rc):
+        if rc != 0:
+            raise HermiteError(rc, lib().hermite_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hermite_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def nodes(self, grid):
+        return int(lib().hermite_nodes(self._h, grid))
+
+    @property
+    def half_steps(self):
+        return int(lib().hermite_half_steps(self._h))
+
+    @property
+    def time(self):
+        return float(lib().hermite_time(self._h))
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(lib().hermite_set_stream(self._h, raw))
+
+    def set_state(self, u, v=None):
+        self._check(lib().hermite_set_state(self._h, _ptr(u), _ptr(v)))
+
+    def set_state_device(self, u, v=None):
+        self._check(lib().hermite_set_state_device(self._h, _ptr(u), _ptr(v)))
+
+    def set_state2(self, u_primal, u_dual):
+        self._check(lib().hermite_set_state2(self._h, _ptr(u_primal), _ptr(u_dual)))
+
+    def step(self, n=1):
+        self._check(lib().hermite_step(self._h, int(n)))
+
+    def advance_half(self, n=1):
+        self._check(lib().hermite_advance_half(self._h, int(n)))
+
+    def _alloc(self, grid):
+        n = self.nodes(grid)
+        return np.empty((n, self.Nu)), (np.empty((n, self.Nv)) if self.variant != CONSERVATIVE else None)
+
+    def get_state(self, out_u=None, out_v=None):
+        u, v = (out_u, out_v) if out_u is not None else self._alloc(PRIMAL)
+        self._check(lib().hermite_get_state(self._h, _ptr(u), _ptr(v)))
+        return u, v
+
+    def get_grid(self, grid):
+        u, v = self._alloc(grid)
+        self._check(lib().hermite_get_grid(self._h, grid, _ptr(u), _ptr(v)))
+        return u, v
+
+    def get_grid_device(self, grid, u, v=None):
+        self._check(lib().hermite_get_grid_device(self._h, grid, _ptr(u), _ptr(v)))
+
+    def set_grid(self, grid, u, v=None):
+        self._check(lib().hermite_set_grid(self._h, grid, _ptr(u), _ptr(v)))
+
+    def energy(self):
+        out = (ctypes.c_double * 3)()
+        self._check(lib().hermite_energy(self._h, out))
+        return np.array(out[:])
+
+    def operator(self, which=0):
+        r, c = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().hermite_operator(self._h, which, None, ctypes.byref(r), ctypes.byref(c)))
+        M = np.empty((r.value, c.value))
+        self._check(lib().hermite_operator(self._h, which, _ptr(M), ctypes.byref(r), ctypes.byref(c)))
+        return M

@@ -1,0 +1,411 @@
+// C ABI of the Hermite library (declarations and contracts: include/hermite.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "hermite_internal.h"
+
+namespace hermite {
+
+bool cuda_ok(hermite_ctx *ctx, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return true;
+  if (ctx) ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+}  // namespace hermite
+
+using namespace hermite;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(hermite_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int64_t ipow64(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+bool supported(int d, int m) {
+  if (d == 1) return m <= 12;
+  if (d == 2) return m <= 6;
+  return m <= 3;
+}
+
+void release(hermite_ctx *ctx) {
+  for (int g = 0; g < 2; ++g) cudaFree(ctx->grid[g]);
+  cudaFree(ctx->M);
+  cudaFree(ctx->Mstart);
+  for (int f = 0; f < kNumForms; ++f) cudaFree(ctx->Q[f]);
+  cudaFree(ctx->par_in);
+  cudaFree(ctx->staging);
+  cudaFree(ctx->scratch_grid);
+  cudaFree(ctx->partials);
+  cudaFree(ctx->result);
+}
+
+bool is_cons(const hermite_ctx *ctx) { return ctx->variant == HERMITE_CONSERVATIVE; }
+
+// grid holding the newest level
+int newest_grid(const hermite_ctx *ctx) {
+  if (is_cons(ctx)) return (ctx->half % 2 == 0) ? HERMITE_DUAL : HERMITE_PRIMAL;
+  return (ctx->half % 2 == 0) ? HERMITE_PRIMAL : HERMITE_DUAL;
+}
+
+int one_half_step(hermite_ctx *ctx) {
+  int rc;
+  if (is_cons(ctx)) {
+    const int dst = (ctx->half % 2 == 0) ? HERMITE_PRIMAL : HERMITE_DUAL;
+    rc = launch_half_step(ctx, dst, ctx->M, ctx->nci, ctx->nco, ctx->grid[1 - dst], ctx->grid[dst], true);
+  } else {
+    const int dst = (ctx->half % 2 == 0) ? HERMITE_DUAL : HERMITE_PRIMAL;
+    rc = launch_half_step(ctx, dst, ctx->M, ctx->nci, ctx->nco, ctx->grid[1 - dst], ctx->grid[dst], false);
+  }
+  if (rc == HERMITE_OK) ctx->half += 1;
+  return rc;
+}
+
+// host [node][coef] buffers -> device SoA grid (through the staging buffer)
+int upload_grid(hermite_ctx *ctx, int grid, const double *u, const double *v, bool device_src) {
+  const int64_t nodes = ctx->nodes[grid];
+  const bool with_v = !is_cons(ctx) && ctx->Nv > 0;
+  double *su = ctx->staging;
+  double *sv = ctx->staging + nodes * ctx->Nu;
+  const cudaMemcpyKind kind = device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (nodes * ctx->Nu > 0 &&
+      !cuda_ok(ctx, cudaMemcpyAsync(su, u, sizeof(double) * nodes * ctx->Nu, kind, ctx->stream), "copy u"))
+    return HERMITE_ERR_CUDA;
+  const double *vsrc = nullptr;
+  if (with_v && v) {
+    if (!cuda_ok(ctx, cudaMemcpyAsync(sv, v, sizeof(double) * nodes * ctx->Nv, kind, ctx->stream), "copy v"))
+      return HERMITE_ERR_CUDA;
+    vsrc = sv;
+  }
+  int rc = launch_to_device_layout(ctx, su, vsrc, grid, nodes, ctx->grid[grid], ctx->ld[grid], ctx->Nu, with_v);
+  if (rc) return rc;
+  if (!device_src && !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "upload sync")) return HERMITE_ERR_CUDA;
+  return HERMITE_OK;
+}
+
+int download_grid(hermite_ctx *ctx, int grid, double *u, double *v, bool device_dst) {
+  const int64_t nodes = ctx->nodes[grid];
+  const bool want_v = !is_cons(ctx) && ctx->Nv > 0 && v != nullptr;
+  double *su = ctx->staging;
+  double *sv = ctx->staging + nodes * ctx->Nu;
+  int rc = launch_to_host_layout(ctx, ctx->grid[grid], ctx->ld[grid], nodes, su, sv, want_v);
+  if (rc) return rc;
+  const cudaMemcpyKind kind = device_dst ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (u && nodes * ctx->Nu > 0 &&
+      !cuda_ok(ctx, cudaMemcpyAsync(u, su, sizeof(double) * nodes * ctx->Nu, kind, ctx->stream), "copy u out"))
+    return HERMITE_ERR_CUDA;
+  if (want_v &&
+      !cuda_ok(ctx, cudaMemcpyAsync(v, sv, sizeof(double) * nodes * ctx->Nv, kind, ctx->stream), "copy v out"))
+    return HERMITE_ERR_CUDA;
+  if (!cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "download sync")) return HERMITE_ERR_CUDA;
+  return HERMITE_OK;
+}
+
+// conservative start-up: dual level at dt/2 from the primal (u, v) data held
+// in the scratch grid as SoA planes (u then (h/c) v)
+int cons_startup(hermite_ctx *ctx, const double *u, const double *v, bool device_src) {
+  const int64_t nodes = ctx->nodes[0];
+  double *su = ctx->staging;
+  double *sv = ctx->staging + nodes * ctx->Nu;
+  const cudaMemcpyKind kind = device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!cuda_ok(ctx, cudaMemcpyAsync(su, u, sizeof(double) * nodes * ctx->Nu, kind, ctx->stream), "copy u"))
+    return HERMITE_ERR_CUDA;
+  const bool with_v = ctx->Nv > 0;
+  if (with_v) {
+    if (v) {
+      if (!cuda_ok(ctx, cudaMemcpyAsync(sv, v, sizeof(double) * nodes * ctx->Nv, kind, ctx->stream), "copy v"))
+        return HERMITE_ERR_CUDA;
+    } else if (!cuda_ok(ctx, cudaMemsetAsync(sv, 0, sizeof(double) * nodes * ctx->Nv, ctx->stream), "zero v")) {
+      return HERMITE_ERR_CUDA;
+    }
+  }
+  // primal u -> grid 0; (u, v) -> scratch SoA with Nu+Nv planes
+  int rc = launch_to_device_layout(ctx, su, nullptr, 0, nodes, ctx->grid[0], ctx->ld[0], ctx->Nu, false);
+  if (rc) return rc;
+  rc = launch_to_device_layout(ctx, su, with_v ? sv : nullptr, 0, nodes, ctx->scratch_grid, ctx->ld[0], ctx->Nu,
+                               with_v);
+  if (rc) return rc;
+  rc = launch_half_step(ctx, HERMITE_DUAL, ctx->Mstart, ctx->Nu + ctx->Nv, ctx->Nu, ctx->scratch_grid,
+                        ctx->grid[1], false);
+  if (rc) return rc;
+  if (!device_src && !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "startup sync")) return HERMITE_ERR_CUDA;
+  return HERMITE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hermite_create(int d, int m, int64_t N, double c, double h, double dt, int variant, int bc,
+                   hermite_ctx **out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return HERMITE_ERR_ARG;
+  }
+  *out = nullptr;
+  const bool cons = variant == HERMITE_CONSERVATIVE;
+  if (d < 1 || d > 3 || N < 1 || !(c > 0) || !(h > 0) || !(dt > 0) || !std::isfinite(c) ||
+      !std::isfinite(h) || !std::isfinite(dt) ||
+      (variant != HERMITE_DISSIPATIVE && variant != HERMITE_CONSERVATIVE &&
+       variant != HERMITE_DISSIPATIVE_SIMPLE) ||
+      (bc != HERMITE_PERIODIC && bc != HERMITE_DIRICHLET && bc != HERMITE_NEUMANN) || (cons ? m < 0 : m < 1)) {
+    g_create_error = "invalid argument to hermite_create";
+    return HERMITE_ERR_ARG;
+  }
+  const double lam = c * dt / h;
+  if (!(lam > 0) || lam > 1.0 + 1e-12) {
+    g_create_error = "CFL number c*dt/h must lie in (0, 1]";
+    return HERMITE_ERR_ARG;
+  }
+  if (!supported(d, m)) {
+    g_create_error = "(d, m) outside the compiled range";
+    return HERMITE_ERR_UNSUPPORTED;
+  }
+  hermite_ctx *ctx = new (std::nothrow) hermite_ctx;
+  if (!ctx) {
+    g_create_error = "host allocation failed";
+    return HERMITE_ERR_ALLOC;
+  }
+  ctx->d = d;
+  ctx->m = m;
+  ctx->variant = variant;
+  ctx->bc = bc;
+  ctx->N = N;
+  ctx->c = c;
+  ctx->h = h;
+  ctx->dt = dt;
+  ctx->lam = lam;
+  ctx->Nu = (int)ipow64(m + 1, d);
+  ctx->Nv = (int)ipow64(m, d);
+  ctx->ncoef = cons ? ctx->Nu : ctx->Nu + ctx->Nv;
+  ctx->nci = ctx->ncoef;
+  ctx->nco = ctx->ncoef;
+  for (int g = 0; g < 2; ++g) {
+    ctx->npts[g] = (bc == HERMITE_PERIODIC) ? N : (g == 0 ? N + 1 : N);
+    ctx->nodes[g] = ipow64(ctx->npts[g], d);
+    ctx->ld[g] = (ctx->nodes[g] + 31) / 32 * 32;
+  }
+  cudaGetDevice(&ctx->device);
+  int rc = HERMITE_OK;
+  const int64_t maxnodes = std::max(ctx->nodes[0], ctx->nodes[1]);
+  const int64_t maxld = std::max(ctx->ld[0], ctx->ld[1]);
+  auto alloc = [&](void **p, size_t bytes, const char *what) {
+    if (rc) return;
+    if (!cuda_ok(ctx, cudaMalloc(p, bytes ? bytes : 8), what)) rc = HERMITE_ERR_ALLOC;
+  };
+  for (int g = 0; g < 2; ++g) alloc((void **)&ctx->grid[g], sizeof(double) * ctx->ncoef * ctx->ld[g], "grid");
+  alloc((void **)&ctx->M, sizeof(double) * ctx->nco * ctx->nci, "operator");
+  alloc((void **)&ctx->staging, sizeof(double) * maxnodes * (ctx->Nu + ctx->Nv), "staging");
+  if (cons) {
+    alloc((void **)&ctx->Mstart, sizeof(double) * ctx->Nu * (ctx->Nu + ctx->Nv), "startup operator");
+    alloc((void **)&ctx->scratch_grid, sizeof(double) * (ctx->Nu + ctx->Nv) * maxld, "scratch grid");
+  }
+  ctx->partials_len = 148 * 8 * (1 << d);
+  alloc((void **)&ctx->partials, sizeof(double) * ctx->partials_len, "partials");
+  alloc((void **)&ctx->result, sizeof(double) * 8, "result");
+  for (int g = 0; g < 2 && rc == HERMITE_OK; ++g)
+    if (!cuda_ok(ctx, cudaMemset(ctx->grid[g], 0, sizeof(double) * ctx->ncoef * ctx->ld[g]), "memset"))
+      rc = HERMITE_ERR_CUDA;
+  if (rc == HERMITE_OK) rc = build_parity_tables(ctx);
+  if (rc == HERMITE_OK) rc = build_operator(ctx, false, ctx->M, ctx->nco, ctx->nci);
+  if (rc == HERMITE_OK && cons) rc = build_operator(ctx, true, ctx->Mstart, ctx->Nu, ctx->Nu + ctx->Nv);
+  if (rc == HERMITE_OK) rc = build_energy_forms(ctx);
+  if (rc == HERMITE_OK && !cuda_ok(ctx, cudaDeviceSynchronize(), "create sync")) rc = HERMITE_ERR_CUDA;
+  if (rc != HERMITE_OK) {
+    g_create_error = ctx->err.empty() ? "hermite_create failed" : ctx->err;
+    release(ctx);
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return HERMITE_OK;
+}
+
+void hermite_destroy(hermite_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  release(ctx);
+  delete ctx;
+}
+
+int hermite_set_stream(hermite_ctx *ctx, void *stream) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return HERMITE_OK;
+}
+
+static int set_state_impl(hermite_ctx *ctx, const double *u, const double *v, bool device_src) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if (!u) return fail(ctx, HERMITE_ERR_ARG, "u is NULL");
+  int rc;
+  if (is_cons(ctx)) {
+    rc = cons_startup(ctx, u, v, device_src);
+  } else {
+    rc = upload_grid(ctx, HERMITE_PRIMAL, u, v, device_src);
+  }
+  if (rc == HERMITE_OK) ctx->half = 0;
+  return rc;
+}
+
+int hermite_set_state(hermite_ctx *ctx, const double *u, const double *v) {
+  return set_state_impl(ctx, u, v, false);
+}
+
+int hermite_set_state_device(hermite_ctx *ctx, const double *u, const double *v) {
+  return set_state_impl(ctx, u, v, true);
+}
+
+int hermite_set_state2(hermite_ctx *ctx, const double *u_primal, const double *u_dual) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if (!is_cons(ctx)) return fail(ctx, HERMITE_ERR_STATE, "hermite_set_state2 is for the conservative method");
+  if (!u_primal || !u_dual) return fail(ctx, HERMITE_ERR_ARG, "NULL level");
+  int rc = upload_grid(ctx, HERMITE_PRIMAL, u_primal, nullptr, false);
+  if (rc == HERMITE_OK) rc = upload_grid(ctx, HERMITE_DUAL, u_dual, nullptr, false);
+  if (rc == HERMITE_OK) ctx->half = 0;
+  return rc;
+}
+
+int hermite_step(hermite_ctx *ctx, int64_t nsteps) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if (nsteps < 0) return fail(ctx, HERMITE_ERR_ARG, "nsteps < 0");
+  return hermite_advance_half(ctx, 2 * nsteps);
+}
+
+int hermite_advance_half(hermite_ctx *ctx, int64_t nhalf) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if (nhalf < 0) return fail(ctx, HERMITE_ERR_ARG, "nhalf < 0");
+  for (int64_t i = 0; i < nhalf; ++i) {
+    int rc = one_half_step(ctx);
+    if (rc) return rc;
+  }
+  return HERMITE_OK;
+}
+
+int64_t hermite_half_steps(const hermite_ctx *ctx) { return ctx ? ctx->half : -1; }
+
+double hermite_time(const hermite_ctx *ctx) {
+  if (!ctx) return NAN;
+  if (is_cons(ctx)) return (double)((ctx->half + 1) / 2) * ctx->dt;
+  return (double)ctx->half * 0.5 * ctx->dt;
+}
+
+int hermite_get_state(hermite_ctx *ctx, double *u, double *v) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if (!u) return fail(ctx, HERMITE_ERR_ARG, "u is NULL");
+  if (!is_cons(ctx) && ctx->half % 2 != 0)
+    return fail(ctx, HERMITE_ERR_STATE, "the newest dissipative level is on the dual grid");
+  return download_grid(ctx, HERMITE_PRIMAL, u, v, false);
+}
+
+int hermite_get_grid(hermite_ctx *ctx, int grid, double *u, double *v) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if ((grid != 0 && grid != 1) || !u) return fail(ctx, HERMITE_ERR_ARG, "bad grid or NULL u");
+  return download_grid(ctx, grid, u, v, false);
+}
+
+int hermite_get_grid_device(hermite_ctx *ctx, int grid, double *u, double *v) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if ((grid != 0 && grid != 1) || !u) return fail(ctx, HERMITE_ERR_ARG, "bad grid or NULL u");
+  return download_grid(ctx, grid, u, v, true);
+}
+
+int hermite_set_grid(hermite_ctx *ctx, int grid, const double *u, const double *v) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if ((grid != 0 && grid != 1) || !u) return fail(ctx, HERMITE_ERR_ARG, "bad grid or NULL u");
+  return upload_grid(ctx, grid, u, v, false);
+}
+
+int hermite_energy(hermite_ctx *ctx, double out[3]) {
+  if (!ctx || !out) return ctx ? fail(ctx, HERMITE_ERR_ARG, "out is NULL") : HERMITE_ERR_ARG;
+  int rc = HERMITE_OK;
+  double host[4] = {0, 0, 0, 0};
+  if (!is_cons(ctx)) {
+    const int g = newest_grid(ctx);
+    rc = launch_energy_form(ctx, 0, g, ctx->grid[g], ctx->grid[g], ctx->result + 0);
+    if (!rc) rc = launch_energy_form(ctx, 1, g, ctx->grid[g], ctx->grid[g], ctx->result + 1);
+  } else {
+    // G = |p_new|^2 - <p_next, p_old>: p_next is the tentative update of the
+    // older level's grid, formed in the scratch grid
+    const int gnew = newest_grid(ctx), gold = 1 - gnew;
+    const size_t bytes = sizeof(double) * ctx->Nu * ctx->ld[gold];
+    if (!cuda_ok(ctx, cudaMemcpyAsync(ctx->scratch_grid, ctx->grid[gold], bytes, cudaMemcpyDeviceToDevice,
+                                      ctx->stream),
+                 "copy level"))
+      return HERMITE_ERR_CUDA;
+    rc = launch_half_step(ctx, gold, ctx->M, ctx->nci, ctx->nco, ctx->grid[gnew], ctx->scratch_grid, true);
+    if (!rc) rc = launch_energy_form(ctx, 0, gnew, ctx->grid[gnew], ctx->grid[gnew], ctx->result + 0);
+    if (!rc) rc = launch_energy_form(ctx, 0, gold, ctx->scratch_grid, ctx->grid[gold], ctx->result + 1);
+    if (!rc) rc = launch_energy_form(ctx, 1, 0, ctx->grid[0], ctx->grid[0], ctx->result + 2);
+  }
+  if (rc) return rc;
+  if (!cuda_ok(ctx, cudaMemcpyAsync(host, ctx->result, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->stream),
+               "energy copy") ||
+      !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "energy sync"))
+    return HERMITE_ERR_CUDA;
+  if (is_cons(ctx)) {
+    out[0] = host[2];
+    out[1] = host[0] - host[1];
+  } else {
+    out[0] = host[0];
+    out[1] = host[1];
+  }
+  out[2] = 0.0;
+  if (!std::isfinite(out[0]) || !std::isfinite(out[1]))
+    return fail(ctx, HERMITE_ERR_NONFINITE, "non-finite energy");
+  return HERMITE_OK;
+}
+
+int64_t hermite_nodes(const hermite_ctx *ctx, int grid) {
+  if (!ctx || (grid != 0 && grid != 1)) return -1;
+  return ctx->nodes[grid];
+}
+
+int hermite_ncoef(const hermite_ctx *ctx, int *nu, int *nv) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if (nu) *nu = ctx->Nu;
+  if (nv) *nv = ctx->Nv;
+  return HERMITE_OK;
+}
+
+int hermite_operator(hermite_ctx *ctx, int which, double *out, int *rows, int *cols) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  const double *src;
+  int r, c;
+  if (which == 0) {
+    src = ctx->M;
+    r = ctx->nco;
+    c = ctx->nci;
+  } else if (which == 1 && is_cons(ctx)) {
+    src = ctx->Mstart;
+    r = ctx->Nu;
+    c = ctx->Nu + ctx->Nv;
+  } else {
+    return fail(ctx, HERMITE_ERR_ARG, "no such operator");
+  }
+  if (rows) *rows = r;
+  if (cols) *cols = c;
+  if (!out) return HERMITE_OK;
+  if (!cuda_ok(ctx, cudaMemcpy(out, src, sizeof(double) * r * c, cudaMemcpyDeviceToHost), "operator copy"))
+    return HERMITE_ERR_CUDA;
+  return HERMITE_OK;
+}
+
+const char *hermite_last_error(const hermite_ctx *ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

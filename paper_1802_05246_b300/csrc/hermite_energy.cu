@@ -1,0 +1,191 @@
+// FP64 energy reduction (Sec. 3.2 Eq. stable1, Sec. 3.3 Eq. stable2,
+// Sec. 4.2).  Each cell's energy is an exact integral of products of its
+// interpolant polynomials, i.e. a quadratic (or bilinear) form in the corner
+// data.  After the Walsh-Hadamard transform over corners the form splits into
+// 2^d parity classes:  E_cell = sum_c y_c(A)^T Q_c y_c(B),
+// y_c[b] = z_{c ^ par(b)}[b].  Q_c is built once per context by the set-up
+// kernels.  Block partial sums are reduced in a fixed order (bit-reproducible).
+#include <algorithm>
+
+#include "hermite_internal.h"
+
+namespace hermite {
+namespace {
+
+constexpr int kEThreads = 64;
+
+template <int D>
+__device__ __forceinline__ void cell_corners_e(const Geometry &g, int64_t t, int64_t *idx, int *gmask,
+                                               double *weight) {
+  int64_t ti[D];
+  int64_t r = t;
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i) {
+    ti[i] = r % g.n_dst;
+    r /= g.n_dst;
+  }
+  double w = 1.0;
+  int64_t si[D][2];
+  int gh[D][2];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    // a cell centred on a boundary primal node is cut in half by the boundary
+    if (g.bc != HERMITE_PERIODIC && g.dst == 0 && (ti[i] == 0 || ti[i] == g.n_dst - 1)) w *= 0.5;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int64_t s = g.dst == 1 ? ti[i] + b : ti[i] - 1 + b;
+      int ghost = 0;
+      if (g.bc == HERMITE_PERIODIC) {
+        if (s < 0) s += g.n_src;
+        if (s >= g.n_src) s -= g.n_src;
+      } else if (s < 0) {
+        s = 0;
+        ghost = 1;
+      } else if (s >= g.n_src) {
+        s = g.n_src - 1;
+        ghost = 1;
+      }
+      si[i][b] = s;
+      gh[i][b] = ghost;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < (1 << D); ++s) {
+    int64_t id = 0;
+    int mask = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const int bit = (s >> (D - 1 - i)) & 1;
+      id = id * g.n_src + si[i][bit];
+      if (gh[i][bit]) mask |= 1 << (D - 1 - i);
+    }
+    idx[s] = id;
+    gmask[s] = mask;
+  }
+  *weight = w;
+}
+
+__device__ __forceinline__ double gsign(int bc, int mask, int pb) {
+  int neg = __popc(mask & pb) & 1;
+  if (bc == HERMITE_DIRICHLET) neg ^= __popc(mask) & 1;
+  return neg ? -1.0 : 1.0;
+}
+
+// class-c component of the corner Walsh-Hadamard transform of coefficient b
+template <int D>
+__device__ __forceinline__ double class_value(const double *__restrict__ plane, const int64_t *idx, const int *gm,
+                                              int bc, int pb, int q) {
+  double acc = 0.0;
+#pragma unroll
+  for (int s = 0; s < (1 << D); ++s) {
+    double v = __ldg(plane + idx[s]);
+    if (gm[s]) v *= gsign(bc, gm[s], pb);
+    acc += (__popc(q & s) & 1) ? -v : v;
+  }
+  return acc;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kEThreads) energy_kernel(Geometry g, const double *__restrict__ Q, int nq,
+                                                           const int8_t *__restrict__ par,
+                                                           const double *__restrict__ A,
+                                                           const double *__restrict__ B, double *partials) {
+  extern __shared__ double sm[];
+  const int c = blockIdx.y;
+  double *Qs = sm;                              // [nq][nq]
+  double *yb = Qs + (size_t)nq * nq;            // [nq][kEThreads]
+  int8_t *pin = reinterpret_cast<int8_t *>(yb + (size_t)nq * kEThreads);
+  __shared__ double red[kEThreads];
+  const double *Qc = Q + (size_t)c * nq * nq;
+  for (int i = threadIdx.x; i < nq * nq; i += kEThreads) Qs[i] = Qc[i];
+  for (int i = threadIdx.x; i < nq; i += kEThreads) pin[i] = par[i];
+  __syncthreads();
+  double total = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * kEThreads;
+  for (int64_t t = (int64_t)blockIdx.x * kEThreads + threadIdx.x; t < g.nodes_dst; t += stride) {
+    int64_t idx[1 << D];
+    int gm[1 << D];
+    double w;
+    cell_corners_e<D>(g, t, idx, gm, &w);
+    for (int b = 0; b < nq; ++b)
+      yb[b * kEThreads + threadIdx.x] =
+          class_value<D>(B + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
+    double cell = 0.0;
+    for (int b = 0; b < nq; ++b) {
+      const double ya =
+          (A == B) ? yb[b * kEThreads + threadIdx.x]
+                   : class_value<D>(A + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
+      if (ya == 0.0) continue;
+      const double *qrow = Qs + (size_t)b * nq;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int k = 0;
+      for (; k + 3 < nq; k += 4) {
+        s0 = fma(qrow[k], yb[k * kEThreads + threadIdx.x], s0);
+        s1 = fma(qrow[k + 1], yb[(k + 1) * kEThreads + threadIdx.x], s1);
+        s2 = fma(qrow[k + 2], yb[(k + 2) * kEThreads + threadIdx.x], s2);
+        s3 = fma(qrow[k + 3], yb[(k + 3) * kEThreads + threadIdx.x], s3);
+      }
+      for (; k < nq; ++k) s0 = fma(qrow[k], yb[k * kEThreads + threadIdx.x], s0);
+      cell = fma(ya, (s0 + s1) + (s2 + s3), cell);
+    }
+    total = fma(w, cell, total);
+  }
+  red[threadIdx.x] = total;
+  __syncthreads();
+  for (int off = kEThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// single-block fixed-order sum of n partials, scaled
+__global__ void reduce_kernel(const double *partials, int64_t n, double scale, double *out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) acc += partials[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = scale * red[0];
+}
+
+template <int D>
+int launch_energy_d(hermite_ctx *ctx, const Geometry &g, int form, const double *A, const double *B,
+                    double *result_slot) {
+  const int nq = ctx->nq[form];
+  const size_t smem = sizeof(double) * ((size_t)nq * nq + (size_t)nq * kEThreads) + nq + 16;
+  static thread_local int configured_dev = -1;
+  if (configured_dev != ctx->device) {
+    if (!cuda_ok(ctx,
+                 cudaFuncSetAttribute(energy_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
+                 "cudaFuncSetAttribute energy"))
+      return HERMITE_ERR_CUDA;
+    configured_dev = ctx->device;
+  }
+  const int nclass = 1 << D;
+  int64_t blocks = std::max<int64_t>(1, (g.nodes_dst + kEThreads - 1) / kEThreads);
+  blocks = std::min<int64_t>(blocks, ctx->partials_len / nclass);
+  dim3 grid((unsigned)blocks, (unsigned)nclass);
+  energy_kernel<D><<<grid, kEThreads, smem, ctx->stream>>>(g, ctx->Q[form], nq, ctx->par_in, A, B, ctx->partials);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, blocks * nclass, ctx->formscale[form], result_slot);
+  return cuda_ok(ctx, cudaGetLastError(), "energy_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+}  // namespace
+
+int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const double *B, double *result_slot) {
+  // cells of a level held on grid g are centred at the nodes of grid 1-g
+  const Geometry geo = make_geometry(ctx, 1 - g);
+  switch (ctx->d) {
+    case 1: return launch_energy_d<1>(ctx, geo, form, A, B, result_slot);
+    case 2: return launch_energy_d<2>(ctx, geo, form, A, B, result_slot);
+    case 3: return launch_energy_d<3>(ctx, geo, form, A, B, result_slot);
+  }
+  return HERMITE_ERR_ARG;
+}
+
+}  // namespace hermite

@@ -1,0 +1,84 @@
+// Internal declarations of the Hermite CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hermite.h"
+
+namespace hermite {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxCoef = 255;   // coefficients per node handled by the kernels
+constexpr int kMaxBox = 512;    // (2m+2)^d polynomial box held in setup kernels
+constexpr int kNumForms = 2;    // energy quadratic forms per context
+
+// Geometry of one half-step or one energy pass: target nodes live on grid
+// `dst`, the cell centred at each target takes its 2^d corners from grid
+// 1-dst (with ghosts for non-periodic boundaries).
+struct Geometry {
+  int d;
+  int bc;
+  int dst;             // 0 primal, 1 dual
+  int64_t n_dst;       // nodes per axis of the target grid
+  int64_t n_src;       // nodes per axis of the source grid
+  int64_t nodes_dst;   // n_dst^d
+  int64_t ld_src;      // plane stride (elements) of the source SoA array
+  int64_t ld_dst;      // plane stride of the target SoA array
+};
+
+}  // namespace hermite
+
+struct hermite_ctx {
+  int d = 0, m = 0, variant = 0, bc = 0;
+  int64_t N = 0;
+  double c = 0, h = 0, dt = 0, lam = 0;
+  int Nu = 0, Nv = 0;      // u / v coefficients per node
+  int ncoef = 0;           // coefficients stored per node (Nu+Nv or Nu)
+  int nci = 0, nco = 0;    // operator inputs / outputs
+  int64_t npts[2] = {0, 0}, nodes[2] = {0, 0}, ld[2] = {0, 0};
+  double *grid[2] = {nullptr, nullptr};   // SoA [ncoef][ld], v stored as (h/c) v
+  double *M = nullptr;                     // half-step operator [nco][nci]
+  double *Mstart = nullptr;                // conservative start-up [Nu][Nu+Nv]
+  double *Q[hermite::kNumForms] = {nullptr, nullptr};  // energy forms [2^d][nq][nq]
+  int nq[hermite::kNumForms] = {0, 0};
+  double formscale[hermite::kNumForms] = {0, 0};
+  int8_t *par_in = nullptr;    // parity bits of each operator input coefficient
+  int8_t *par_out = nullptr;   // parity bits of each operator output coefficient
+  double *staging = nullptr;   // host-layout staging [max nodes][Nu+Nv]
+  double *scratch_grid = nullptr;  // one grid of u (conservative energy)
+  double *partials = nullptr;      // energy block partial sums
+  double *result = nullptr;        // energy results (device)
+  int64_t partials_len = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t half = 0;            // half-steps since the state was set
+  std::string err;
+};
+
+namespace hermite {
+
+// Setup kernels (FP64, hermite_setup.cu).
+int build_operator(hermite_ctx *ctx, bool startup, double *out, int rows, int cols);
+int build_energy_forms(hermite_ctx *ctx);
+int build_parity_tables(hermite_ctx *ctx);
+
+// Hot path (hermite_step.cu).
+int launch_half_step(hermite_ctx *ctx, int dst, const double *M, int nci, int nco,
+                     const double *src, double *dst_arr, bool subtract_old);
+int launch_to_device_layout(hermite_ctx *ctx, const double *host_layout_u,
+                            const double *host_layout_v, int grid, int64_t nodes,
+                            double *soa, int64_t ld, int nu_count, bool has_v);
+int launch_to_host_layout(hermite_ctx *ctx, const double *soa, int64_t ld, int64_t nodes,
+                          double *out_u, double *out_v, bool want_v);
+
+// Energy reduction (hermite_energy.cu).
+int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const double *B,
+                       double *result_slot);
+
+Geometry make_geometry(const hermite_ctx *ctx, int dst);
+bool cuda_ok(hermite_ctx *ctx, cudaError_t e, const char *what);
+
+}  // namespace hermite

@@ -1,0 +1,254 @@
+// FP64 fused half-step kernel: gather of the 2^d corner nodes of each cell
+// (with the odd/even ghost polynomials of Sec. 3.1.3 applied on the fly),
+// Walsh-Hadamard transform over the corners, and the per-cell operator that
+// composes Hermite interpolation (Sec. 2.2), exact Taylor evolution
+// (Sec. 3.1.2 / 3.3 / 4.1) and evaluation at the cell centre.
+//
+// Reflection symmetry of a cell gives M_s[a][b] = sign_s(a) sign_s(b) M_0[a][b]
+// for corner s, so with z_q[b] = sum_s (-1)^{|q & s|} x_s[b] one operator row
+// suffices:  out[a] = sum_b M_0[a][b] z_{par(a) ^ par(b)}[b].
+#include <algorithm>
+
+#include "hermite_internal.h"
+
+namespace hermite {
+namespace {
+
+constexpr int kThreads = 128;
+
+template <int D>
+__device__ __forceinline__ void cell_corners(const Geometry &g, int64_t t, int64_t *idx, int *gmask) {
+  int64_t ti[D];
+  int64_t r = t;
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i) {
+    ti[i] = r % g.n_dst;
+    r /= g.n_dst;
+  }
+  int64_t si[D][2];
+  int gh[D][2];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int64_t s = g.dst == 1 ? ti[i] + b : ti[i] - 1 + b;
+      int ghost = 0;
+      if (g.bc == HERMITE_PERIODIC) {
+        if (s < 0) s += g.n_src;
+        if (s >= g.n_src) s -= g.n_src;
+      } else if (s < 0) {
+        s = 0;
+        ghost = 1;
+      } else if (s >= g.n_src) {
+        s = g.n_src - 1;
+        ghost = 1;
+      }
+      si[i][b] = s;
+      gh[i][b] = ghost;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < (1 << D); ++s) {
+    int64_t id = 0;
+    int mask = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const int bit = (s >> (D - 1 - i)) & 1;
+      id = id * g.n_src + si[i][bit];
+      if (gh[i][bit]) mask |= 1 << (D - 1 - i);
+    }
+    idx[s] = id;
+    gmask[s] = mask;
+  }
+}
+
+// Ghost polynomial sign for a coefficient with parity bits pb when the corner
+// is a ghost in the axes of mask: odd extension (Dirichlet) gives
+// (-1)^{k_i+1} per ghost axis, even extension (Neumann) (-1)^{k_i}.
+__device__ __forceinline__ double ghost_sign(int bc, int mask, int pb) {
+  int neg = __popc(mask & pb) & 1;
+  if (bc == HERMITE_DIRICHLET) neg ^= __popc(mask) & 1;
+  return neg ? -1.0 : 1.0;
+}
+
+template <int D>
+__device__ __forceinline__ void wht(double *x) {
+#pragma unroll
+  for (int bm = 1; bm < (1 << D); bm <<= 1)
+#pragma unroll
+    for (int i = 0; i < (1 << D); ++i)
+      if (!(i & bm)) {
+        const double a = x[i], b = x[i | bm];
+        x[i] = a + b;
+        x[i | bm] = a - b;
+      }
+}
+
+template <int D, int CH>
+__global__ void __launch_bounds__(kThreads) half_step_f64_kernel(Geometry g, const double *__restrict__ M,
+                                                                 int nci, int nco,
+                                                                 const int8_t *__restrict__ par,
+                                                                 const double *__restrict__ src,
+                                                                 double *__restrict__ dst, int subtract_old) {
+  extern __shared__ double smem[];
+  constexpr int NC = 1 << D;
+  const int chunk0 = blockIdx.y * CH;
+  double *Ms = smem;                              // [nci][CH]
+  double *zb = Ms + (size_t)nci * CH;             // [NC][kThreads]
+  int8_t *pin = reinterpret_cast<int8_t *>(zb + NC * kThreads);
+  for (int i = threadIdx.x; i < nci * CH; i += kThreads) {
+    const int b = i / CH, j = i % CH, row = chunk0 + j;
+    Ms[i] = row < nco ? M[(size_t)row * nci + b] : 0.0;
+  }
+  for (int i = threadIdx.x; i < nci; i += kThreads) pin[i] = par[i];
+  int po[CH];
+#pragma unroll
+  for (int j = 0; j < CH; ++j) po[j] = (chunk0 + j < nco) ? par[chunk0 + j] : 0;
+  __syncthreads();
+  double *myz = zb + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < g.nodes_dst; t += stride) {
+    int64_t idx[NC];
+    int gm[NC];
+    cell_corners<D>(g, t, idx, gm);
+    double acc[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) acc[j] = 0.0;
+    for (int b = 0; b < nci; ++b) {
+      const double *plane = src + (size_t)b * g.ld_src;
+      const int pb = pin[b];
+      double x[NC];
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        double v = __ldg(plane + idx[s]);
+        if (gm[s]) v *= ghost_sign(g.bc, gm[s], pb);
+        x[s] = v;
+      }
+      wht<D>(x);
+#pragma unroll
+      for (int s = 0; s < NC; ++s) myz[s * kThreads] = x[s];
+      const double *mrow = Ms + (size_t)b * CH;
+#pragma unroll
+      for (int j = 0; j < CH; ++j) acc[j] = fma(mrow[j], myz[(po[j] ^ pb) * kThreads], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int row = chunk0 + j;
+      if (row < nco) {
+        double *o = dst + (size_t)row * g.ld_dst + t;
+        *o = subtract_old ? acc[j] - *o : acc[j];
+      }
+    }
+  }
+}
+
+template <int D, int CH>
+int launch_dch(hermite_ctx *ctx, const Geometry &g, const double *M, int nci, int nco, const double *src,
+               double *dst, bool sub) {
+  auto kern = half_step_f64_kernel<D, CH>;
+  const size_t smem = sizeof(double) * ((size_t)nci * CH + (1 << D) * kThreads) + nci + 16;
+  static thread_local int configured_dev = -1;
+  if (configured_dev != ctx->device) {
+    if (!cuda_ok(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                 "cudaFuncSetAttribute"))
+      return HERMITE_ERR_CUDA;
+    configured_dev = ctx->device;
+  }
+  if (g.nodes_dst == 0) return HERMITE_OK;
+  const int chunks = (nco + CH - 1) / CH;
+  int64_t blocks = (g.nodes_dst + kThreads - 1) / kThreads;
+  blocks = std::min<int64_t>(blocks, 148 * 64);
+  dim3 grid((unsigned)blocks, (unsigned)chunks);
+  kern<<<grid, kThreads, smem, ctx->stream>>>(g, M, nci, nco, ctx->par_in, src, dst, sub ? 1 : 0);
+  return cuda_ok(ctx, cudaGetLastError(), "half_step_f64_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+template <int D>
+int launch_d(hermite_ctx *ctx, const Geometry &g, const double *M, int nci, int nco, const double *src,
+             double *dst, bool sub) {
+  if (nco <= 16) return launch_dch<D, 16>(ctx, g, M, nci, nco, src, dst, sub);
+  if (nco <= 32) return launch_dch<D, 32>(ctx, g, M, nci, nco, src, dst, sub);
+  if (nco <= 64) return launch_dch<D, 64>(ctx, g, M, nci, nco, src, dst, sub);
+  return launch_dch<D, 96>(ctx, g, M, nci, nco, src, dst, sub);
+}
+
+// host layout [node][coef] (u block then v block) <-> SoA planes [coef][ld];
+// the velocity is held as (h/c) v on the device.
+__global__ void to_soa_kernel(const double *__restrict__ hu, const double *__restrict__ hv, int64_t nodes,
+                              int nu, int nv, double vscale, double *__restrict__ soa, int64_t ld) {
+  const int64_t total = nodes * (nu + nv);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / nodes, node = i % nodes;
+    double v;
+    if (k < nu)
+      v = hu[node * nu + k];
+    else
+      v = hv ? vscale * hv[node * nv + (k - nu)] : 0.0;
+    soa[k * ld + node] = v;
+  }
+}
+
+__global__ void from_soa_kernel(const double *__restrict__ soa, int64_t ld, int64_t nodes, int nu, int nv,
+                                double vscale, double *__restrict__ hu, double *__restrict__ hv) {
+  const int64_t total = nodes * (nu + nv);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = i / (nu + nv), k = i % (nu + nv);
+    const double v = soa[k * ld + node];
+    if (k < nu)
+      hu[node * nu + k] = v;
+    else
+      hv[node * nv + (k - nu)] = vscale * v;
+  }
+}
+
+}  // namespace
+
+Geometry make_geometry(const hermite_ctx *ctx, int dst) {
+  Geometry g;
+  g.d = ctx->d;
+  g.bc = ctx->bc;
+  g.dst = dst;
+  g.n_dst = ctx->npts[dst];
+  g.n_src = ctx->npts[1 - dst];
+  g.nodes_dst = ctx->nodes[dst];
+  g.ld_src = ctx->ld[1 - dst];
+  g.ld_dst = ctx->ld[dst];
+  return g;
+}
+
+int launch_half_step(hermite_ctx *ctx, int dst, const double *M, int nci, int nco, const double *src,
+                     double *dst_arr, bool subtract_old) {
+  const Geometry g = make_geometry(ctx, dst);
+  switch (ctx->d) {
+    case 1: return launch_d<1>(ctx, g, M, nci, nco, src, dst_arr, subtract_old);
+    case 2: return launch_d<2>(ctx, g, M, nci, nco, src, dst_arr, subtract_old);
+    case 3: return launch_d<3>(ctx, g, M, nci, nco, src, dst_arr, subtract_old);
+  }
+  return HERMITE_ERR_ARG;
+}
+
+int launch_to_device_layout(hermite_ctx *ctx, const double *hu, const double *hv, int grid, int64_t nodes,
+                            double *soa, int64_t ld, int nu_count, bool has_v) {
+  (void)grid;
+  const int nv = has_v ? ctx->Nv : 0;
+  const int64_t total = nodes * (nu_count + nv);
+  if (total == 0) return HERMITE_OK;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
+  to_soa_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(hu, hv, nodes, nu_count, nv, ctx->h / ctx->c, soa, ld);
+  return cuda_ok(ctx, cudaGetLastError(), "to_soa_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+int launch_to_host_layout(hermite_ctx *ctx, const double *soa, int64_t ld, int64_t nodes, double *hu,
+                          double *hv, bool want_v) {
+  const int nv = want_v ? ctx->Nv : 0;
+  const int64_t total = nodes * (ctx->Nu + nv);
+  if (total == 0) return HERMITE_OK;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
+  from_soa_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(soa, ld, nodes, ctx->Nu, nv, ctx->c / ctx->h, hu,
+                                                             hv);
+  return cuda_ok(ctx, cudaGetLastError(), "from_soa_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+}  // namespace hermite
