@@ -147,10 +147,12 @@ int hermite_energy(hermite_ctx *ctx, double out[3]);
 int64_t hermite_nodes(const hermite_ctx *ctx, int grid);
 int hermite_ncoef(const hermite_ctx *ctx, int *nu, int *nv);
 
-/* Copy the FP64 per-cell operator of the reference corner (all axes at
- * xi = -1/2): rows = outputs (u then (h/c) v, or u only), columns = inputs
- * (u then (h/c) v).  which = 0: half-step operator; 1: conservative start-up
- * operator.  rows/cols receive the sizes; out may be NULL to query them. */
+/* Copy the FP64 per-cell operator of the reference corner (every axis at
+ * xi = -1/2), row-major: rows = outputs (u then v, or u only), columns =
+ * inputs (u then v, or u only), both in the paper's scaled units.  The other
+ * corners follow by reflection.  which = 0: half-step operator; 1:
+ * conservative start-up operator.  rows/cols receive the sizes; out may be
+ * NULL to query them. */
 int hermite_operator(hermite_ctx *ctx, int which, double *out, int *rows, int *cols);
 
 /* Message of the last failed call on this context ("" if none).  With a NULL

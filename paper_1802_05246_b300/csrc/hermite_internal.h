@@ -39,7 +39,7 @@ struct hermite_ctx {
   int ncoef = 0;           // coefficients stored per node (Nu+Nv or Nu)
   int nci = 0, nco = 0;    // operator inputs / outputs
   int64_t npts[2] = {0, 0}, nodes[2] = {0, 0}, ld[2] = {0, 0};
-  double *grid[2] = {nullptr, nullptr};   // SoA [ncoef][ld], v stored as (h/c) v
+  double *grid[2] = {nullptr, nullptr};   // SoA [ncoef][ld] of the paper's scaled data
   double *M = nullptr;                     // half-step operator [nco][nci]
   double *Mstart = nullptr;                // conservative start-up [Nu][Nu+Nv]
   double *Q[hermite::kNumForms] = {nullptr, nullptr};  // energy forms [2^d][nq][nq]

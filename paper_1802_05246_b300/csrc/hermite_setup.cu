@@ -59,7 +59,7 @@ __global__ void basis_kernel(int q, double *H) {
       for (int i = n - 1; i >= 1; --i) s[i] -= s[i - 1];
     for (int j = 0; j < n; ++j) {
       double acc = 0.0;
-      for (int i = j; i < n; ++i) acc += s[i] * dbinom(i, j) * pow(0.5, (double)(i - j));
+      for (int i = j; i < n; ++i) acc += s[i] * dbinom(i, j) * ldexp(1.0, -(i - j));  // exact 2^-(i-j)
       H[j * (q + 1) + l] = acc;
     }
   }
@@ -135,6 +135,9 @@ struct OpParams {
   PolySpace P;
   int variant, startup, Nu, Nv, nci, nco;
   double tau;
+  double vscale;  // h/c: the series act on (h/c) v; columns of v inputs are
+                  // multiplied by h/c and rows of v outputs by c/h so that the
+                  // operator maps the paper's (u, v) data directly
   double *work;  // [nci][8][B]
   double *out;   // [nco][nci]
 };
@@ -150,6 +153,7 @@ __global__ void operator_kernel(OpParams p) {
   for (int k = 0; k < 5 * B; ++k) w[k] = 0.0;
   const bool cons = (p.variant == HERMITE_CONSERVATIVE) && !p.startup;
   const bool is_u = beta < p.Nu;
+  const double colscale = is_u ? 1.0 : p.vscale;
   int b[kMaxDim] = {0, 0, 0};
   unravel(d, is_u ? m + 1 : m, is_u ? beta : beta - p.Nu, b);
   int qm[kMaxDim] = {m, m, m}, qv[kMaxDim] = {m - 1, m - 1, m - 1};
@@ -219,13 +223,13 @@ __global__ void operator_kernel(OpParams p) {
   for (int row = 0; row < p.Nu; ++row) {
     int a[kMaxDim] = {0, 0, 0};
     unravel(d, m + 1, row, a);
-    p.out[(size_t)row * p.nci + beta] = U[ravel(d, P.E, a)];
+    p.out[(size_t)row * p.nci + beta] = colscale * U[ravel(d, P.E, a)];
   }
   if (!p.startup)
     for (int row = 0; row < p.Nv; ++row) {
       int a[kMaxDim] = {0, 0, 0};
       unravel(d, m, row, a);
-      p.out[(size_t)(p.Nu + row) * p.nci + beta] = V[ravel(d, P.E, a)];
+      p.out[(size_t)(p.Nu + row) * p.nci + beta] = (colscale / p.vscale) * V[ravel(d, P.E, a)];
     }
 }
 
@@ -243,6 +247,7 @@ enum FormKind { kDissPlain = 0, kDissInvariant = 1, kConsSemi = 2, kConsGrad = 3
 struct FormParams {
   PolySpace P;
   int kind, Nu, Nv, nq, ncomp, nclass;
+  double vscale;  // h/c: v data enter the forms as (h/c) v
   double *F;   // [nclass][nq][ncomp][B] component polynomials
   double *HF;  // same with the monomial Gram matrix applied per axis
   double *work;  // [nclass*nq][4][B]
@@ -263,7 +268,7 @@ __device__ void restrict_class(const PolySpace &P, int c, double *f) {
 }
 
 // int_{-1/2}^{1/2} xi^n dxi
-__device__ inline double moment(int n) { return (n & 1) ? 0.0 : pow(0.5, (double)n) / (n + 1); }
+__device__ inline double moment(int n) { return (n & 1) ? 0.0 : ldexp(1.0, -n) / (n + 1); }
 
 __device__ void gram_apply(const PolySpace &P, const double *f, double *out, double *tmp) {
   for (int k = 0; k < P.B; ++k) out[k] = f[k];
@@ -290,7 +295,7 @@ __global__ void form_components_kernel(FormParams p) {
   const PolySpace &P = p.P;
   const int B = P.B, d = P.d, m = P.m;
   double *w = p.work + (size_t)id * 4 * B;
-  double *a = w, *t1 = w + B, *t2 = w + 2 * B, *t3 = w + 3 * B;
+  double *a = w, *t1 = w + B, *t3 = w + 3 * B;
   const bool is_u = beta < p.Nu;
   int b[kMaxDim] = {0, 0, 0};
   unravel(d, is_u ? m + 1 : m, is_u ? beta : beta - p.Nu, b);
@@ -334,8 +339,9 @@ __global__ void form_components_kernel(FormParams p) {
       }
       for (int k = 0; k < B; ++k) F[k] = a[k];
     }
+    if (!is_u)
+      for (int k = 0; k < B; ++k) F[k] *= p.vscale;
     gram_apply(P, F, HF, t3);
-    (void)t2;
   }
 }
 
@@ -407,6 +413,7 @@ int build_operator(hermite_ctx *ctx, bool startup, double *out, int rows, int co
     p.nci = cols;
     p.nco = rows;
     p.tau = 0.5 * ctx->lam;
+    p.vscale = ctx->h / ctx->c;
     p.out = out;
     if (!cuda_ok(ctx, cudaMalloc(&work, sizeof(double) * (size_t)cols * 8 * p.P.B), "cudaMalloc work")) {
       rc = HERMITE_ERR_ALLOC;
@@ -455,6 +462,7 @@ int build_energy_forms(hermite_ctx *ctx) {
       p.nq = nq;
       p.ncomp = ncomp;
       p.nclass = nclass;
+      p.vscale = ctx->h / ctx->c;
       p.F = F;
       p.HF = HF;
       p.work = work;

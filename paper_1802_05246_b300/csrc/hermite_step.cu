@@ -172,8 +172,8 @@ int launch_d(hermite_ctx *ctx, const Geometry &g, const double *M, int nci, int 
   return launch_dch<D, 96>(ctx, g, M, nci, nco, src, dst, sub);
 }
 
-// host layout [node][coef] (u block then v block) <-> SoA planes [coef][ld];
-// the velocity is held as (h/c) v on the device.
+// host layout [node][coef] (u block then v block) <-> SoA planes [coef][ld]
+// (values copied unchanged: the device holds the paper's scaled data).
 __global__ void to_soa_kernel(const double *__restrict__ hu, const double *__restrict__ hv, int64_t nodes,
                               int nu, int nv, double vscale, double *__restrict__ soa, int64_t ld) {
   const int64_t total = nodes * (nu + nv);
@@ -236,7 +236,7 @@ int launch_to_device_layout(hermite_ctx *ctx, const double *hu, const double *hv
   const int64_t total = nodes * (nu_count + nv);
   if (total == 0) return HERMITE_OK;
   const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
-  to_soa_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(hu, hv, nodes, nu_count, nv, ctx->h / ctx->c, soa, ld);
+  to_soa_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(hu, hv, nodes, nu_count, nv, 1.0, soa, ld);
   return cuda_ok(ctx, cudaGetLastError(), "to_soa_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
@@ -246,8 +246,7 @@ int launch_to_host_layout(hermite_ctx *ctx, const double *soa, int64_t ld, int64
   const int64_t total = nodes * (ctx->Nu + nv);
   if (total == 0) return HERMITE_OK;
   const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
-  from_soa_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(soa, ld, nodes, ctx->Nu, nv, ctx->c / ctx->h, hu,
-                                                             hv);
+  from_soa_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(soa, ld, nodes, ctx->Nu, nv, 1.0, hu, hv);
   return cuda_ok(ctx, cudaGetLastError(), "from_soa_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
