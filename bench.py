@@ -1,0 +1,304 @@
+"""Benchmark: Hermite DOF-updates/s on one B300 (replicas for N > 1).
+
+Workload (the 3-D grid the throughput target is quoted on): periodic [0,1]^3,
+m = 3, N = 128 cells per axis (2,097,152 nodes, 64 u + 27 v coefficients per
+node), c dt/h = 0.9, u0 = sum of 8 Gaussian pulses (centres U[0,1)^3, widths
+U[0.05,0.1], amplitudes N(0,1), numpy PCG64 seed 0), v0 = 0, dissipative
+"full" variant, FP64.
+
+One benchmark step = one pass of the whole hot path: 8 full time steps
+(16 fused half-step launches) followed by one energy reduction (the energy
+is a diagnostic taken every 8 steps).  One DOF-update = one stored scaled
+coefficient of one node written by one half-step.  The 3 GB state is far
+larger than the 126 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; each rank runs an independent
+replica (the method needs no data-path collective here), the slowest rank's
+time counts and `value` aggregates all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hermite DOF-updates/s on 1 B300 (FP64 vs split-FP32/BF16) at matched L2 error"
+UNIT = "DOF-updates/s"
+D, M, N, LAM = 3, 3, 128, 0.9
+FULL_STEPS_PER_STEP = 8
+NU, NV = (M + 1) ** D, M ** D
+NODES = N ** D
+DOF_PER_HALF = NODES * (NU + NV)
+WORKLOAD = ("3-D periodic [0,1]^3, m=3, N=128^3, c*dt/h=0.9, 8 seeded Gaussian pulses, v0=0, "
+            "dissipative full variant")
+# algorithmic flops of one node-half-step in the parity-reduced form: one
+# operator row (2*nci multiply-adds) per output plus the corner transform
+FLOP_PER_NODE = 2 * (NU + NV) * (NU + NV) + (NU + NV) * D * (1 << D)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+FP64_NOMINAL_GFLOPS = 148 * 2 * 2 * 2032e6 / 1e9  # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def initial_state():
+    from paper_1802_05246_b300 import inputs as I
+
+    h = 1.0 / N
+    cen, wid, amp = I.pulses_3d_config(0)
+    u0 = I.gaussian_data(D, M, N, h, I.PERIODIC, 0, cen, wid, amp)
+    v0 = np.zeros((NODES, NV))
+    return u0, v0
+
+
+def cpu_baseline_sample(u0, v0, n_targets, seed=1):
+    """The oracle, as it stands, on a bounded sample of the workload: one
+    half-step for n_targets random dual nodes.  Returns (DOF-updates/s, seconds)."""
+    import oracle
+
+    h = 1.0 / N
+    P = oracle.Problem(D, M, N, 1.0, h, LAM * h, oracle.DISSIPATIVE, oracle.PERIODIC)
+    t = np.random.default_rng(seed).integers(0, NODES, n_targets)
+    t0 = time.perf_counter()
+    P.half_step_sample(1, u0, v0, t)
+    dt = time.perf_counter() - t0
+    return n_targets * (NU + NV) / dt, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    u0, v0 = initial_state()
+    n_targets = 2048
+    for _ in range(args.warmup):
+        cpu_baseline_sample(u0, v0, 256)
+    times, vals = [], []
+    for k in range(args.steps):
+        v, dt = cpu_baseline_sample(u0, v0, n_targets, seed=10 + k)
+        vals.append(v)
+        times.append(dt)
+    value = n_targets * (NU + NV) * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{n_targets} random dual nodes, one half-step each"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_targets} random target nodes x {args.steps} steps of one half-step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1802_05246_b300 as hb
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h = 1.0 / N
+    u0, v0 = initial_state()
+    g = hb.Hermite(D, M, N, 1.0, h, LAM * h, hb.DISSIPATIVE, hb.PERIODIC)
+    stream = torch.cuda.Stream(device=dev)
+    g.set_stream(stream)
+    du = torch.from_numpy(u0).to(dev)
+    dv = torch.from_numpy(v0).to(dev)
+    torch.cuda.synchronize()
+    g.set_state_device(du, dv)
+
+    launches_per_step = 2 * FULL_STEPS_PER_STEP + 4  # 16 half-steps + 2 x (energy + reduce)
+
+    def one_step(events=None):
+        for _ in range(2 * FULL_STEPS_PER_STEP):
+            g.advance_half(1)
+            if events is not None:
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(stream)
+                events.append(ev)
+        return g.energy()  # synchronises the stream
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    half_events = []
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            evs = [ev0]
+            energy = one_step(evs)
+            half_events.append(evs)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    halfs = [a.elapsed_time(b) for evs in half_events for a, b in zip(evs[:-1], evs[1:])]
+    half_ms = sum(halfs) / len(halfs)
+    dof_per_step = 2 * FULL_STEPS_PER_STEP * DOF_PER_HALF
+    value = ws * dof_per_step * args.steps / (ms / 1e3)
+
+    # end to end through the public API with host buffers: H2D of the state,
+    # the step, and D2H of the state and the energy
+    hu = torch.from_numpy(u0).pin_memory()
+    hv = torch.from_numpy(v0).pin_memory()
+    ou = torch.empty_like(hu).pin_memory()
+    ov = torch.empty_like(hv).pin_memory()
+    g.set_state(hu.numpy(), hv.numpy())
+    one_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.set_state(hu.numpy(), hv.numpy())
+        one_step()
+        g.get_state(ou.numpy(), ov.numpy())
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = ws * dof_per_step / e2e_s
+    state_bytes = NODES * (NU + NV) * 8
+
+    if rank != 0:
+        g.close()
+        return 0
+    pk = peaks()
+    flops_per_launch = NODES * FLOP_PER_NODE
+    achieved = flops_per_launch / (half_ms / 1e3) / 1e12
+    cpu_v, cpu_s = cpu_baseline_sample(u0, v0, 4096) if ws == 1 else (None, None)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "d": D, "m": M, "N": N, "cfl": LAM, "variant": "dissipative",
+                   "bc": "periodic", "step": "8 full time steps (16 half-steps) + 1 energy reduction",
+                   "l2": "inputs larger than L2 (3.05 GB read+written per half-step vs 126 MB)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "kernel": "half_step_f64_kernel<3,96>", "achieved": achieved,
+                     "peak": FP64_NOMINAL_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": achieved / (FP64_NOMINAL_GFLOPS / 1e3),
+                     "peak_source": "FP64 nominal from unit counts and clocks (148 SMs x 2 DFMA/clk x 2032 MHz); "
+                                    "MEASURED_PEAKS.json has no FP64 entry",
+                     "flop_per_launch": flops_per_launch, "launch_ms": half_ms,
+                     "hbm_GBps_equiv": 2 * DOF_PER_HALF * 8 / (half_ms / 1e3) / 1e9,
+                     "hbm_peak_GBps": pk.get("hbm_gbs"),
+                     "traffic": None},
+        "cpu_baseline": ({"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                          "sample": f"4096 random dual nodes of the same grid, one half-step ({cpu_s:.1f} s)"}
+                         if cpu_v else None),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes + 24},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "energy_last": [float(x) for x in energy],
+    }
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
