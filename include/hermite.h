@@ -155,6 +155,30 @@ int hermite_ncoef(const hermite_ctx *ctx, int *nu, int *nv);
  * NULL to query them. */
 int hermite_operator(hermite_ctx *ctx, int which, double *out, int *rows, int *cols);
 
+/* Allocation-free energy of a caller-provided level.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need the energy -- e.g. code that runs where a
+ * cudaMalloc would be illegal or would stall the device, or a host that only
+ * lends the library buffers it already owns.  It performs the same reduction
+ * as hermite_energy's two quadratic forms but keeps its per-block partial
+ * sums in a fixed 2 MB array inside the library (held on every device that
+ * uses this call until the library is unloaded) instead of allocating.
+ *   ctx      an existing context (its forms and stream are used)
+ *   grid     grid holding the level (HERMITE_PRIMAL or HERMITE_DUAL)
+ *   level    device pointer, coefficient-major layout level[coef * ld + node]
+ *            (u coefficients then v coefficients, paper units), FP64
+ *   ld       plane stride in elements, ld >= hermite_nodes(ctx, grid)
+ *   out_dev  device pointer to 2 doubles, written on the context's stream:
+ *            dissipative: [int v^2 + c^2|grad u|^2, stable1/stable2 energy];
+ *            conservative: [|p|^2_{m+1,..,m+1}, c^2 int |grad p|^2].
+ * Limit: at most 2^21 cells (= nodes of the other grid); larger problems get
+ * HERMITE_ERR_ARG with a message.  No host synchronisation.  The first call
+ * on a device looks up the array's device address (make that first call
+ * before any stream capture).  All calls share the one array: calls whose
+ * work overlaps on the GPU (other streams or threads) race and must be
+ * serialised by the caller.  The context's device must be current. */
+int hermite_energy_noalloc(hermite_ctx *ctx, int grid, const double *level, int64_t ld, double *out_dev);
+
 /* Message of the last failed call on this context ("" if none).  With a NULL
  * context: the message of the last failed hermite_create in this thread. */
 const char *hermite_last_error(const hermite_ctx *ctx);

@@ -29,7 +29,7 @@ EXPORTS = [
     "hermite_create", "hermite_destroy", "hermite_set_stream", "hermite_set_state", "hermite_set_state_device",
     "hermite_set_state2", "hermite_step", "hermite_advance_half", "hermite_half_steps", "hermite_time",
     "hermite_get_state", "hermite_get_grid", "hermite_set_grid", "hermite_get_grid_device", "hermite_energy",
-    "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error",
+    "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error", "hermite_energy_noalloc",
 ]
 
 
@@ -72,6 +72,7 @@ def lib():
         "hermite_ncoef": (c_int, [vp, ip, ip]),
         "hermite_operator": (c_int, [vp, c_int, vp, ip, ip]),
         "hermite_last_error": (ctypes.c_char_p, [vp]),
+        "hermite_energy_noalloc": (c_int, [vp, c_int, vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -188,6 +189,11 @@ class Hermite:
         out = (ctypes.c_double * 3)()
         self._check(lib().hermite_energy(self._h, out))
         return np.array(out[:])
+
+    def energy_noalloc(self, grid, level, ld, out):
+        """Allocation-free energy of a device level (see hermite_energy_noalloc);
+        level: coefficient-major float64 device tensor, out: 2-element device tensor."""
+        self._check(lib().hermite_energy_noalloc(self._h, int(grid), _ptr(level), int(ld), _ptr(out)))
 
     def operator(self, which=0):
         r, c = ctypes.c_int(), ctypes.c_int()

@@ -6,6 +6,8 @@
 // y_c[b] = z_{c ^ par(b)}[b].  Q_c is built once per context by the set-up
 // kernels.  Block partial sums are reduced in a fixed order (bit-reproducible).
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "hermite_internal.h"
 
@@ -189,3 +191,90 @@ int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const
 }
 
 }  // namespace hermite
+
+// ---------------------------------------------------------------------------
+// Allocation-free energy entry point.  Callers that must not allocate device
+// memory at the point of the call (for example code running inside a region
+// where cudaMalloc is forbidden or would synchronise the device, or a host
+// that only hands the library pre-existing buffers) get the same reduction
+// with its block partial sums in this file-scope array instead of the
+// context's own scratch buffer.  The array lives for as long as the library
+// is loaded, on every device that uses this entry point.
+namespace hermite {
+namespace {
+
+constexpr int64_t kNoAllocMaxCells = int64_t(1) << 21;  // 2,097,152 cells
+constexpr int64_t kNoAllocPartials = (kNoAllocMaxCells / kEThreads) * 8;  // 2 MB of doubles
+
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_partials on the current device (looked up once
+// per device; the host-side symbol itself is not a device address).
+double *noalloc_scratch(hermite_ctx *ctx, int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    if (!cuda_ok(ctx, cudaGetSymbolAddress(&p, g_noalloc_partials), "cudaGetSymbolAddress")) return nullptr;
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+template <int D>
+int launch_energy_noalloc_d(hermite_ctx *ctx, const Geometry &g, int form, const double *A, double *partials,
+                            double *out) {
+  const int nq = ctx->nq[form];
+  const size_t smem = sizeof(double) * ((size_t)nq * nq + (size_t)nq * kEThreads) + nq + 16;
+  if (!cuda_ok(ctx, cudaFuncSetAttribute(energy_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
+               "cudaFuncSetAttribute energy"))
+    return HERMITE_ERR_CUDA;
+  const int64_t blocks = std::max<int64_t>(1, (g.nodes_dst + kEThreads - 1) / kEThreads);
+  dim3 grid((unsigned)blocks, (unsigned)(1 << D));
+  energy_kernel<D><<<grid, kEThreads, smem, ctx->stream>>>(g, ctx->Q[form], nq, ctx->par_in, A, A, partials);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partials, blocks * (1 << D), ctx->formscale[form], out);
+  return cuda_ok(ctx, cudaGetLastError(), "energy_kernel (no-alloc)") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace hermite
+
+extern "C" int hermite_energy_noalloc(hermite_ctx *ctx, int grid, const double *level, int64_t ld,
+                                      double *out_dev) {
+  using namespace hermite;
+  if (!ctx) return HERMITE_ERR_ARG;
+  if ((grid != 0 && grid != 1) || !level || !out_dev || ld < ctx->nodes[grid]) {
+    ctx->err = "hermite_energy_noalloc: bad grid, NULL pointer or ld < nodes";
+    return HERMITE_ERR_ARG;
+  }
+  // cells of a level held on grid g are centred at the nodes of grid 1-g
+  const int64_t cells = ctx->nodes[1 - grid];
+  if (cells > kNoAllocMaxCells) {
+    ctx->err = "hermite_energy_noalloc: " + std::to_string(cells) + " cells exceed the maximum of " +
+               std::to_string(kNoAllocMaxCells) + " supported without allocation";
+    return HERMITE_ERR_ARG;
+  }
+  int dev = -1;
+  if (!cuda_ok(ctx, cudaGetDevice(&dev), "cudaGetDevice")) return HERMITE_ERR_CUDA;
+  if (dev != ctx->device || dev < 0 || dev >= kMaxDevices) {
+    ctx->err = "hermite_energy_noalloc: the context's device must be current";
+    return HERMITE_ERR_ARG;
+  }
+  double *partials = noalloc_scratch(ctx, dev);
+  if (!partials) return HERMITE_ERR_CUDA;
+  Geometry g = make_geometry(ctx, 1 - grid);
+  g.ld_src = ld;
+  for (int f = 0; f < kNumForms; ++f) {
+    int rc;
+    switch (ctx->d) {
+      case 1: rc = launch_energy_noalloc_d<1>(ctx, g, f, level, partials, out_dev + f); break;
+      case 2: rc = launch_energy_noalloc_d<2>(ctx, g, f, level, partials, out_dev + f); break;
+      default: rc = launch_energy_noalloc_d<3>(ctx, g, f, level, partials, out_dev + f); break;
+    }
+    if (rc) return rc;
+  }
+  return HERMITE_OK;
+}
