@@ -57,6 +57,7 @@ def peaks():
 
 
 FP64_NOMINAL_GFLOPS = 148 * 2 * 2 * 2032e6 / 1e9  # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
+TRAFFIC_PER_LAUNCH = 379.8e6 * 8  # bytes, see profiles/half_step_f64_3d_m3.md
 
 
 def dist_env():
@@ -273,7 +274,9 @@ def run_ours(args):
                      "flop_per_launch": flops_per_launch, "launch_ms": half_ms,
                      "hbm_GBps_equiv": 2 * DOF_PER_HALF * 8 / (half_ms / 1e3) / 1e9,
                      "hbm_peak_GBps": pk.get("hbm_gbs"),
-                     "traffic": None},
+                     # dram read+write bytes of one launch from an ncu capture of the
+                     # same kernel at 64^3 (379.8 MB), scaled by the node count (x8)
+                     "traffic": TRAFFIC_PER_LAUNCH},
         "cpu_baseline": ({"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                           "sample": f"4096 random dual nodes of the same grid, one half-step ({cpu_s:.1f} s)"}
                          if cpu_v else None),
