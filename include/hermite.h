@@ -77,6 +77,22 @@ enum {
 int hermite_create(int d, int m, int64_t N, double c, double h, double dt,
                    int variant, int bc, hermite_ctx **out);
 
+/* Arithmetic of the half-step kernels.
+ *   HERMITE_FP64     state and arithmetic in IEEE double precision.
+ *   HERMITE_SPLIT32  state and operator as unevaluated sums of two FP32 numbers
+ *                    (hi + lo, about 48 significant bits); every multiply-add
+ *                    is formed from three split products (hi*hi exactly, hi*lo,
+ *                    lo*hi) with error-free compensated accumulation on the
+ *                    FP32 pipe.  Energies stay FP64 reductions. */
+enum { HERMITE_FP64 = 0, HERMITE_SPLIT32 = 1 };
+
+/* hermite_create with a choice of arithmetic (HERMITE_FP64 or
+ * HERMITE_SPLIT32); same arguments, contracts and errors otherwise.  A split
+ * context also keeps FP64 copies of both grids for I/O and energies (twice
+ * the device memory of an FP64 context). */
+int hermite_create_ex(int d, int m, int64_t N, double c, double h, double dt,
+                      int variant, int bc, int precision, hermite_ctx **out);
+
 /* Release all device memory of the context (NULL is ignored). */
 void hermite_destroy(hermite_ctx *ctx);
 

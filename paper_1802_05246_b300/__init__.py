@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libhermite_b300.so")
 DISSIPATIVE, CONSERVATIVE, DISSIPATIVE_SIMPLE = 0, 1, 2
 PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
 PRIMAL, DUAL = 0, 1
+FP64, SPLIT32 = 0, 1
 
 ERRORS = {
     -1: "HERMITE_ERR_ARG", -2: "HERMITE_ERR_ALLOC", -3: "HERMITE_ERR_CUDA", -4: "HERMITE_ERR_NONFINITE",
@@ -30,6 +31,7 @@ EXPORTS = [
     "hermite_set_state2", "hermite_step", "hermite_advance_half", "hermite_half_steps", "hermite_time",
     "hermite_get_state", "hermite_get_grid", "hermite_set_grid", "hermite_get_grid_device", "hermite_energy",
     "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error", "hermite_energy_noalloc",
+    "hermite_create_ex",
 ]
 
 
@@ -73,6 +75,7 @@ def lib():
         "hermite_operator": (c_int, [vp, c_int, vp, ip, ip]),
         "hermite_last_error": (ctypes.c_char_p, [vp]),
         "hermite_energy_noalloc": (c_int, [vp, c_int, vp, i64, vp]),
+        "hermite_create_ex": (c_int, [c_int, c_int, i64, c_dbl, c_dbl, c_dbl, c_int, c_int, c_int, ctypes.POINTER(vp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -99,16 +102,16 @@ def _ptr(a):
 class Hermite:
     """One problem on the current CUDA device (see ``hermite_create``)."""
 
-    def __init__(self, d, m, N, c, h, dt, variant=DISSIPATIVE, bc=PERIODIC):
+    def __init__(self, d, m, N, c, h, dt, variant=DISSIPATIVE, bc=PERIODIC, precision=FP64):
         L = lib()
         h_ = ctypes.c_void_p()
-        rc = L.hermite_create(int(d), int(m), int(N), float(c), float(h), float(dt), int(variant), int(bc),
-                              ctypes.byref(h_))
+        rc = L.hermite_create_ex(int(d), int(m), int(N), float(c), float(h), float(dt), int(variant), int(bc),
+                                 int(precision), ctypes.byref(h_))
         if rc != 0:
             raise HermiteError(rc, L.hermite_last_error(None).decode())
         self._h = h_
         self.d, self.m, self.N, self.c, self.h, self.dt = int(d), int(m), int(N), float(c), float(h), float(dt)
-        self.variant, self.bc = int(variant), int(bc)
+        self.variant, self.bc, self.precision = int(variant), int(bc), int(precision)
         nu, nv = ctypes.c_int(), ctypes.c_int()
         L.hermite_ncoef(self._h, ctypes.byref(nu), ctypes.byref(nv))
         self.Nu, self.Nv = nu.value, nv.value

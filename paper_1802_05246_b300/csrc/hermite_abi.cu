@@ -51,6 +51,33 @@ void release(hermite_ctx *ctx) {
   cudaFree(ctx->scratch_grid);
   cudaFree(ctx->partials);
   cudaFree(ctx->result);
+  for (int g = 0; g < 2; ++g) cudaFree(ctx->fgrid[g]);
+  cudaFree(ctx->Mc);
+  cudaFree(ctx->outrow);
+  cudaFree(ctx->npc);
+}
+
+bool is_split(const hermite_ctx *ctx) { return ctx->precision == HERMITE_SPLIT32; }
+
+// split precision: refresh the FP32 hi/lo state from the FP64 copies, or the
+// FP64 copies from the state
+int sync_split_from_fp64(hermite_ctx *ctx) {
+  if (!is_split(ctx)) return HERMITE_OK;
+  for (int g = 0; g < 2; ++g) {
+    int rc = split_from_fp64(ctx, g);
+    if (rc) return rc;
+  }
+  return HERMITE_OK;
+}
+
+int sync_fp64_from_split(hermite_ctx *ctx, int grid) {
+  if (!is_split(ctx)) return HERMITE_OK;
+  for (int g = 0; g < 2; ++g) {
+    if (grid >= 0 && g != grid) continue;
+    int rc = split_to_fp64(ctx, g);
+    if (rc) return rc;
+  }
+  return HERMITE_OK;
 }
 
 bool is_cons(const hermite_ctx *ctx) { return ctx->variant == HERMITE_CONSERVATIVE; }
@@ -63,7 +90,11 @@ int newest_grid(const hermite_ctx *ctx) {
 
 int one_half_step(hermite_ctx *ctx) {
   int rc;
-  if (is_cons(ctx)) {
+  if (is_split(ctx)) {
+    const int dst = is_cons(ctx) ? ((ctx->half % 2 == 0) ? HERMITE_PRIMAL : HERMITE_DUAL)
+                                 : ((ctx->half % 2 == 0) ? HERMITE_DUAL : HERMITE_PRIMAL);
+    rc = launch_half_step_split(ctx, dst, is_cons(ctx));
+  } else if (is_cons(ctx)) {
     const int dst = (ctx->half % 2 == 0) ? HERMITE_PRIMAL : HERMITE_DUAL;
     rc = launch_half_step(ctx, dst, ctx->M, ctx->nci, ctx->nco, ctx->grid[1 - dst], ctx->grid[dst], true);
   } else {
@@ -97,6 +128,7 @@ int upload_grid(hermite_ctx *ctx, int grid, const double *u, const double *v, bo
 }
 
 int download_grid(hermite_ctx *ctx, int grid, double *u, double *v, bool device_dst) {
+  if (int rc = sync_fp64_from_split(ctx, grid)) return rc;
   const int64_t nodes = ctx->nodes[grid];
   const bool want_v = !is_cons(ctx) && ctx->Nv > 0 && v != nullptr;
   double *su = ctx->staging;
@@ -151,6 +183,16 @@ extern "C" {
 
 int hermite_create(int d, int m, int64_t N, double c, double h, double dt, int variant, int bc,
                    hermite_ctx **out) {
+  return hermite_create_ex(d, m, N, c, h, dt, variant, bc, HERMITE_FP64, out);
+}
+
+int hermite_create_ex(int d, int m, int64_t N, double c, double h, double dt, int variant, int bc,
+                      int precision, hermite_ctx **out) {
+  if (precision != HERMITE_FP64 && precision != HERMITE_SPLIT32) {
+    g_create_error = "unknown precision";
+    if (out) *out = nullptr;
+    return HERMITE_ERR_ARG;
+  }
   if (!out) {
     g_create_error = "out is NULL";
     return HERMITE_ERR_ARG;
@@ -223,6 +265,14 @@ int hermite_create(int d, int m, int64_t N, double c, double h, double dt, int v
   if (rc == HERMITE_OK) rc = build_operator(ctx, false, ctx->M, ctx->nco, ctx->nci);
   if (rc == HERMITE_OK && cons) rc = build_operator(ctx, true, ctx->Mstart, ctx->Nu, ctx->Nu + ctx->Nv);
   if (rc == HERMITE_OK) rc = build_energy_forms(ctx);
+  ctx->precision = precision;
+  if (rc == HERMITE_OK && precision == HERMITE_SPLIT32) {
+    for (int g = 0; g < 2; ++g) alloc((void **)&ctx->fgrid[g], sizeof(float2) * ctx->ncoef * ctx->ld[g], "split grid");
+    for (int g = 0; g < 2 && rc == HERMITE_OK; ++g)
+      if (!cuda_ok(ctx, cudaMemset(ctx->fgrid[g], 0, sizeof(float2) * ctx->ncoef * ctx->ld[g]), "memset"))
+        rc = HERMITE_ERR_CUDA;
+    if (rc == HERMITE_OK) rc = build_split_operator(ctx);
+  }
   if (rc == HERMITE_OK && !cuda_ok(ctx, cudaDeviceSynchronize(), "create sync")) rc = HERMITE_ERR_CUDA;
   if (rc != HERMITE_OK) {
     g_create_error = ctx->err.empty() ? "hermite_create failed" : ctx->err;
@@ -256,6 +306,7 @@ static int set_state_impl(hermite_ctx *ctx, const double *u, const double *v, bo
   } else {
     rc = upload_grid(ctx, HERMITE_PRIMAL, u, v, device_src);
   }
+  if (rc == HERMITE_OK) rc = sync_split_from_fp64(ctx);
   if (rc == HERMITE_OK) ctx->half = 0;
   return rc;
 }
@@ -274,6 +325,7 @@ int hermite_set_state2(hermite_ctx *ctx, const double *u_primal, const double *u
   if (!u_primal || !u_dual) return fail(ctx, HERMITE_ERR_ARG, "NULL level");
   int rc = upload_grid(ctx, HERMITE_PRIMAL, u_primal, nullptr, false);
   if (rc == HERMITE_OK) rc = upload_grid(ctx, HERMITE_DUAL, u_dual, nullptr, false);
+  if (rc == HERMITE_OK) rc = sync_split_from_fp64(ctx);
   if (rc == HERMITE_OK) ctx->half = 0;
   return rc;
 }
@@ -325,12 +377,16 @@ int hermite_get_grid_device(hermite_ctx *ctx, int grid, double *u, double *v) {
 int hermite_set_grid(hermite_ctx *ctx, int grid, const double *u, const double *v) {
   if (!ctx) return HERMITE_ERR_ARG;
   if ((grid != 0 && grid != 1) || !u) return fail(ctx, HERMITE_ERR_ARG, "bad grid or NULL u");
-  return upload_grid(ctx, grid, u, v, false);
+  if (int rc = sync_fp64_from_split(ctx, 1 - grid)) return rc;
+  int rc = upload_grid(ctx, grid, u, v, false);
+  if (rc == HERMITE_OK && is_split(ctx)) rc = split_from_fp64(ctx, grid);
+  return rc;
 }
 
 int hermite_energy(hermite_ctx *ctx, double out[3]) {
   if (!ctx || !out) return ctx ? fail(ctx, HERMITE_ERR_ARG, "out is NULL") : HERMITE_ERR_ARG;
-  int rc = HERMITE_OK;
+  int rc = sync_fp64_from_split(ctx, -1);  // energies are FP64 reductions
+  if (rc) return rc;
   double host[4] = {0, 0, 0, 0};
   if (!is_cons(ctx)) {
     const int g = newest_grid(ctx);

@@ -55,6 +55,14 @@ struct hermite_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   int64_t half = 0;            // half-steps since the state was set
+  // split precision (HERMITE_SPLIT32): state as FP32 hi + lo pairs; the FP64
+  // grids above then serve as the staging copies for I/O and energies
+  int precision = 0;
+  float2 *fgrid[2] = {nullptr, nullptr};  // SoA [ncoef][ld] of (hi, lo)
+  float2 *Mc = nullptr;        // operator rows grouped by output parity class
+  int16_t *outrow = nullptr;   // [2^d][nomax] output row of each class slot (-1 unused)
+  int8_t *npc = nullptr;       // outputs per class
+  int nomax = 0;
   std::string err;
 };
 
@@ -73,6 +81,12 @@ int launch_to_device_layout(hermite_ctx *ctx, const double *host_layout_u,
                             double *soa, int64_t ld, int nu_count, bool has_v);
 int launch_to_host_layout(hermite_ctx *ctx, const double *soa, int64_t ld, int64_t nodes,
                           double *out_u, double *out_v, bool want_v);
+
+// Split precision (hermite_split.cu).
+int build_split_operator(hermite_ctx *ctx);
+int launch_half_step_split(hermite_ctx *ctx, int dst, bool subtract_old);
+int split_from_fp64(hermite_ctx *ctx, int grid);
+int split_to_fp64(hermite_ctx *ctx, int grid);
 
 // Energy reduction (hermite_energy.cu).
 int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const double *B,

@@ -1,0 +1,339 @@
+// Split-precision half-step: state and operator held as unevaluated sums of
+// two FP32 numbers (hi + lo, ~48 significant bits), every multiply-add formed
+// from three split products -- hi*hi exactly (FMA residual), hi*lo, lo*hi --
+// and accumulated with an error-free two-sum.  Same algorithm as the FP64
+// kernel (corner gather with ghost signs, Walsh-Hadamard transform over the
+// 2^d corners, one operator row per output), run on the FP32 pipe.
+//
+// Work split inside a block of 32 target nodes and 2^d warps: in phase A warp
+// w transforms input coefficient b0+w for the 32 nodes and writes its 2^d
+// class components to shared memory; in phase B warp w owns parity class w
+// and accumulates the outputs of that class.  Each corner value is loaded
+// and transformed once per node.
+#include <algorithm>
+#include <vector>
+
+#include "hermite_internal.h"
+
+namespace hermite {
+namespace {
+
+// IEEE round-to-nearest intrinsics keep the compiler from contracting the
+// error-free transformations into FMAs.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float2 t = two_sum(a.x, b.x);
+  t.y = __fadd_rn(t.y, __fadd_rn(a.y, b.y));
+  return t;
+}
+
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float2 df_norm(float2 a) {
+  const float s = __fadd_rn(a.x, a.y);
+  return make_float2(s, __fsub_rn(a.y, __fsub_rn(s, a.x)));
+}
+
+// acc += m * y with three split products and a compensated sum
+__device__ __forceinline__ void df_fma(float2 &acc, const float2 m, const float2 y) {
+  const float p = __fmul_rn(m.x, y.x);
+  const float e = __fmaf_rn(m.x, y.x, -p);
+  const float2 s = two_sum(acc.x, p);
+  float c = __fadd_rn(acc.y, __fadd_rn(s.y, e));
+  c = __fmaf_rn(m.x, y.y, c);
+  c = __fmaf_rn(m.y, y.x, c);
+  acc = make_float2(s.x, c);
+}
+
+template <int D>
+__device__ __forceinline__ void corners_split(const Geometry &g, int64_t t, int64_t *idx, int *gmask) {
+  int64_t ti[D];
+  int64_t r = t;
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i) {
+    ti[i] = r % g.n_dst;
+    r /= g.n_dst;
+  }
+  int64_t si[D][2];
+  int gh[D][2];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int64_t s = g.dst == 1 ? ti[i] + b : ti[i] - 1 + b;
+      int ghost = 0;
+      if (g.bc == HERMITE_PERIODIC) {
+        if (s < 0) s += g.n_src;
+        if (s >= g.n_src) s -= g.n_src;
+      } else if (s < 0) {
+        s = 0;
+        ghost = 1;
+      } else if (s >= g.n_src) {
+        s = g.n_src - 1;
+        ghost = 1;
+      }
+      si[i][b] = s;
+      gh[i][b] = ghost;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < (1 << D); ++s) {
+    int64_t id = 0;
+    int mask = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const int bit = (s >> (D - 1 - i)) & 1;
+      id = id * g.n_src + si[i][bit];
+      if (gh[i][bit]) mask |= 1 << (D - 1 - i);
+    }
+    idx[s] = id;
+    gmask[s] = mask;
+  }
+}
+
+__device__ __forceinline__ bool ghost_negates(int bc, int mask, int pb) {
+  int neg = __popc(mask & pb) & 1;
+  if (bc == HERMITE_DIRICHLET) neg ^= __popc(mask) & 1;
+  return neg != 0;
+}
+
+template <int D, int NOMAX>
+__global__ void __launch_bounds__(32 << D) half_step_split_kernel(
+    Geometry g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow, const int8_t *__restrict__ npc,
+    int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src, float2 *__restrict__ dst,
+    int subtract_old) {
+  constexpr int NC = 1 << D;
+  constexpr int NT = 32 * NC;
+  extern __shared__ float2 sm2[];
+  float2 *Ms = sm2;                               // [NC class][nci][NOMAX]
+  float2 *Ybuf = Ms + (size_t)NC * nci * NOMAX;   // 2 x [NC beta slot][NC class][32]
+  int8_t *pin = reinterpret_cast<int8_t *>(Ybuf + 2 * NC * NC * 32);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < NC * nci * NOMAX; i += NT) Ms[i] = Mc[i];
+  for (int i = threadIdx.x; i < nci; i += NT) pin[i] = par[i];
+  const int np = npc[w];
+  __syncthreads();
+  const int64_t nblk = (g.nodes_dst + 31) / 32;
+  const int nchunks = (nci + NC - 1) / NC;
+  for (int64_t nb = blockIdx.x; nb < nblk; nb += gridDim.x) {
+    const int64_t t = nb * 32 + lane;
+    const bool valid = t < g.nodes_dst;
+    int64_t idx[NC];
+    int gm[NC];
+    if (valid) {
+      corners_split<D>(g, t, idx, gm);
+    } else {
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        idx[s] = 0;
+        gm[s] = 0;
+      }
+    }
+    // phase A for one chunk: warp w transforms coefficient b0 + w into buffer Y
+    auto transform = [&](int b0, float2 *Y) {
+      const int b = b0 + w;
+      if (b >= nci) return;
+      const float2 *plane = src + (size_t)b * g.ld_src;
+      const int pb = pin[b];
+      float2 x[NC];
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        float2 v = plane[idx[s]];
+        if (gm[s] && ghost_negates(g.bc, gm[s], pb)) v = df_neg(v);
+        x[s] = v;
+      }
+#pragma unroll
+      for (int bm = 1; bm < NC; bm <<= 1)
+#pragma unroll
+        for (int i = 0; i < NC; ++i)
+          if (!(i & bm)) {
+            const float2 a = x[i], c = x[i | bm];
+            x[i] = df_add(a, c);
+            x[i | bm] = df_add(a, df_neg(c));
+          }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) Y[(w * NC + q) * 32 + lane] = x[q];
+    };
+    float2 acc[NOMAX];
+#pragma unroll
+    for (int j = 0; j < NOMAX; ++j) acc[j] = make_float2(0.f, 0.f);
+    transform(0, Ybuf);
+    __syncthreads();
+    for (int ch = 0; ch < nchunks; ++ch) {
+      // the next chunk is transformed into the other buffer while this one is
+      // consumed; one barrier per chunk
+      if (ch + 1 < nchunks) transform((ch + 1) * NC, Ybuf + ((ch + 1) & 1) * NC * NC * 32);
+      const float2 *Y = Ybuf + (ch & 1) * NC * NC * 32;
+      const int b0 = ch * NC;
+      const int kmax = min(NC, nci - b0);
+      // every slot runs (unused slots multiply zeros) so that the NOMAX
+      // independent accumulator chains interleave; operator pairs are read
+      // 16 bytes at a time
+      auto consume = [&](int k) {
+        const int bb = b0 + k;
+        const float2 y = Y[(k * NC + (w ^ pin[bb])) * 32 + lane];
+        const float4 *mrow = reinterpret_cast<const float4 *>(Ms + ((size_t)w * nci + bb) * NOMAX);
+#pragma unroll
+        for (int j = 0; j < NOMAX / 2; ++j) {
+          const float4 mm = mrow[j];
+          df_fma(acc[2 * j], make_float2(mm.x, mm.y), y);
+          df_fma(acc[2 * j + 1], make_float2(mm.z, mm.w), y);
+        }
+      };
+      if (kmax == NC) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) consume(k);
+      } else {
+        for (int k = 0; k < kmax; ++k) consume(k);
+      }
+      __syncthreads();
+    }
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < NOMAX; ++j) {
+        if (j < np) {
+          const int row = outrow[w * NOMAX + j];
+          float2 *o = dst + (size_t)row * g.ld_dst + t;
+          float2 r = df_norm(acc[j]);
+          if (subtract_old) r = df_norm(df_add(r, df_neg(*o)));
+          *o = r;
+        }
+      }
+    }
+  }
+}
+
+template <int D, int NOMAX>
+int launch_split_dn(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub) {
+  constexpr int NC = 1 << D;
+  auto kern = half_step_split_kernel<D, NOMAX>;
+  const size_t smem = sizeof(float2) * ((size_t)NC * ctx->nci * NOMAX + 2 * NC * NC * 32) + ctx->nci + 16;
+  static thread_local int configured_dev = -1;
+  if (configured_dev != ctx->device) {
+    if (!cuda_ok(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
+                 "cudaFuncSetAttribute split"))
+      return HERMITE_ERR_CUDA;
+    configured_dev = ctx->device;
+  }
+  if (g.nodes_dst == 0) return HERMITE_OK;
+  const int64_t nblk = (g.nodes_dst + 31) / 32;
+  const int64_t blocks = std::min<int64_t>(nblk, 148 * 16);
+  kern<<<(unsigned)blocks, 32 * NC, smem, ctx->stream>>>(g, ctx->Mc, ctx->outrow, ctx->npc, ctx->nci, ctx->par_in,
+                                                          src, dst, sub ? 1 : 0);
+  return cuda_ok(ctx, cudaGetLastError(), "half_step_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+template <int D>
+int launch_split_d(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub) {
+  if (ctx->nomax <= 8) return launch_split_dn<D, 8>(ctx, g, src, dst, sub);
+  if (ctx->nomax <= 16) return launch_split_dn<D, 16>(ctx, g, src, dst, sub);
+  return launch_split_dn<D, 32>(ctx, g, src, dst, sub);
+}
+
+// operator rows grouped by output parity class, each entry split hi + lo
+__global__ void split_operator_kernel(const double *M, int nci, const int16_t *outrow, int nclass, int nomax,
+                                      float2 *Mc) {
+  const int64_t n = (int64_t)nclass * nci * nomax;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % nomax);
+    const int b = (int)((i / nomax) % nci);
+    const int c = (int)(i / ((int64_t)nomax * nci));
+    const int row = outrow[c * nomax + j];
+    const double m = row >= 0 ? M[(size_t)row * nci + b] : 0.0;
+    const float hi = __double2float_rn(m);
+    Mc[i] = make_float2(hi, __double2float_rn(m - (double)hi));
+  }
+}
+
+__global__ void to_split_kernel(const double *__restrict__ a, int64_t ld, int planes, int64_t nodes,
+                                float2 *__restrict__ out) {
+  const int64_t total = (int64_t)planes * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i % ld >= nodes) continue;
+    const double x = a[i];
+    const float hi = __double2float_rn(x);
+    out[i] = make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+}
+
+__global__ void from_split_kernel(const float2 *__restrict__ a, int64_t ld, int planes, int64_t nodes,
+                                  double *__restrict__ out) {
+  const int64_t total = (int64_t)planes * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i % ld >= nodes) continue;
+    const float2 v = a[i];
+    out[i] = (double)v.x + (double)v.y;
+  }
+}
+
+}  // namespace
+
+int build_split_operator(hermite_ctx *ctx) {
+  const int nclass = 1 << ctx->d;
+  // group output rows by parity class
+  std::vector<int> counts(nclass, 0);
+  std::vector<int8_t> parh(ctx->Nu + ctx->Nv);
+  if (!cuda_ok(ctx, cudaMemcpy(parh.data(), ctx->par_in, parh.size(), cudaMemcpyDeviceToHost), "parity copy"))
+    return HERMITE_ERR_CUDA;
+  for (int r = 0; r < ctx->nco; ++r) counts[parh[r]]++;
+  int nomax = 0;
+  for (int c = 0; c < nclass; ++c) nomax = std::max(nomax, counts[c]);
+  ctx->nomax = nomax <= 8 ? 8 : (nomax <= 16 ? 16 : 32);
+  if (nomax > 32) return HERMITE_ERR_UNSUPPORTED;
+  std::vector<int16_t> outrow((size_t)nclass * ctx->nomax, -1);
+  std::vector<int8_t> npc(nclass, 0);
+  for (int r = 0; r < ctx->nco; ++r) {
+    const int c = parh[r];
+    outrow[(size_t)c * ctx->nomax + npc[c]] = (int16_t)r;
+    npc[c]++;
+  }
+  if (!cuda_ok(ctx, cudaMalloc(&ctx->outrow, sizeof(int16_t) * outrow.size()), "cudaMalloc outrow") ||
+      !cuda_ok(ctx, cudaMalloc(&ctx->npc, nclass), "cudaMalloc npc") ||
+      !cuda_ok(ctx, cudaMalloc(&ctx->Mc, sizeof(float2) * (size_t)nclass * ctx->nci * ctx->nomax), "cudaMalloc Mc"))
+    return HERMITE_ERR_ALLOC;
+  if (!cuda_ok(ctx, cudaMemcpy(ctx->outrow, outrow.data(), sizeof(int16_t) * outrow.size(), cudaMemcpyHostToDevice),
+               "outrow copy") ||
+      !cuda_ok(ctx, cudaMemcpy(ctx->npc, npc.data(), nclass, cudaMemcpyHostToDevice), "npc copy"))
+    return HERMITE_ERR_CUDA;
+  split_operator_kernel<<<64, 256, 0, ctx->stream>>>(ctx->M, ctx->nci, ctx->outrow, nclass, ctx->nomax, ctx->Mc);
+  if (!cuda_ok(ctx, cudaGetLastError(), "split_operator_kernel") ||
+      !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "split operator sync"))
+    return HERMITE_ERR_CUDA;
+  return HERMITE_OK;
+}
+
+int launch_half_step_split(hermite_ctx *ctx, int dst, bool subtract_old) {
+  const Geometry g = make_geometry(ctx, dst);
+  const float2 *src = ctx->fgrid[1 - dst];
+  float2 *out = ctx->fgrid[dst];
+  switch (ctx->d) {
+    case 1: return launch_split_d<1>(ctx, g, src, out, subtract_old);
+    case 2: return launch_split_d<2>(ctx, g, src, out, subtract_old);
+    case 3: return launch_split_d<3>(ctx, g, src, out, subtract_old);
+  }
+  return HERMITE_ERR_ARG;
+}
+
+int split_from_fp64(hermite_ctx *ctx, int grid) {
+  const int64_t total = (int64_t)ctx->ncoef * ctx->ld[grid];
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
+  to_split_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, ctx->stream>>>(
+      ctx->grid[grid], ctx->ld[grid], ctx->ncoef, ctx->nodes[grid], ctx->fgrid[grid]);
+  return cuda_ok(ctx, cudaGetLastError(), "to_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+int split_to_fp64(hermite_ctx *ctx, int grid) {
+  const int64_t total = (int64_t)ctx->ncoef * ctx->ld[grid];
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
+  from_split_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, ctx->stream>>>(
+      ctx->fgrid[grid], ctx->ld[grid], ctx->ncoef, ctx->nodes[grid], ctx->grid[grid]);
+  return cuda_ok(ctx, cudaGetLastError(), "from_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+}  // namespace hermite

@@ -1,0 +1,96 @@
+"""Split-precision path (HERMITE_SPLIT32): parity with the oracle and the
+accuracy bar -- error against the exact solution within 1.2x of the FP64
+path's wherever the FP64 error is at least 1e-9 -- on refinement sweeps of the
+1-D (m = 3, c dt/h = 0.9, T = 1) and 2-D (m = 4, c dt/h = 1, T = 2) standing
+waves.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1802_05246_b300 import inputs as I
+from tests.gpu_util import lib_built, need_gpu, rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL_SPLIT = 1e-10  # relative L2 after the run; hi+lo carries ~48 bits
+
+
+@pytest.fixture(scope="module")
+def hb():
+    need_gpu()
+    return lib_built()
+
+
+@pytest.mark.parametrize("d,m,N,lam,variant,bc,nsteps", [
+    (1, 3, 16, 0.9, 0, 0, 10), (1, 3, 16, 0.9, 1, 0, 10), (2, 4, 10, 1.0, 0, 0, 4), (2, 4, 10, 1.0, 1, 0, 4),
+    (2, 2, 7, 0.8, 2, 1, 3), (3, 3, 5, 0.9, 0, 0, 2), (3, 3, 5, 0.9, 1, 0, 2), (3, 1, 6, 0.9, 0, 2, 3),
+    (2, 6, 5, 0.8, 0, 0, 2), (1, 6, 9, 0.7, 1, 1, 6),
+])
+def test_split_matches_oracle(hb, orc, d, m, N, lam, variant, bc, nsteps):
+    h = 1.0 / N
+    dt = lam * h
+    g = hb.Hermite(d, m, N, 1.0, h, dt, variant, bc, precision=hb.SPLIT32)
+    P = orc.Problem(d, m, N, 1.0, h, dt, variant, bc)
+    rng = np.random.default_rng(d * 7 + m)
+    n0 = P.nnodes(0)
+    u0 = rng.standard_normal((n0, P.Nu))
+    v0 = rng.standard_normal((n0, P.Nv))
+    g.set_state(u0, v0)
+    g.step(nsteps)
+    gu, gv = g.get_state()
+    if variant == orc.CONSERVATIVE:
+        ou, oq = P.run(u0, nsteps=nsteps, dual_u=P.cons_start(u0, v0))
+        assert rel_l2(gu, ou) <= TOL_SPLIT
+        assert rel_l2(g.get_grid(1)[0], oq) <= TOL_SPLIT
+    else:
+        ou, ov = P.run(u0, v0, nsteps=nsteps)
+        assert rel_l2(np.concatenate([gu, gv], 1), np.concatenate([ou, ov], 1)) <= TOL_SPLIT
+
+
+def test_split_energy_matches_fp64(hb):
+    N, m = 8, 3
+    h = 1.0 / N
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal((N ** 3, 64))
+    v = rng.standard_normal((N ** 3, 27))
+    es = []
+    for prec in (hb.FP64, hb.SPLIT32):
+        g = hb.Hermite(3, m, N, 1.0, h, 0.9 * h, 0, 0, precision=prec)
+        g.set_state(u, v)
+        g.step(2)
+        es.append(g.energy())
+    np.testing.assert_allclose(es[1][:2], es[0][:2], rtol=1e-11)
+
+
+def _standing(hb, d, m, N, lam, T, variant, prec):
+    h = 1.0 / N
+    nsteps = math.ceil(T / (lam * h))
+    dt = T / nsteps
+    a = 2 * np.pi
+    if d == 1:
+        u0 = I.sine_data(1, m, N, h, 0, 0, [a])
+        om = a
+    else:
+        u0 = 0.5 * (I.sine_data(2, m, N, h, 0, 0, [a, -a], phase=np.pi / 2)
+                    - I.sine_data(2, m, N, h, 0, 0, [a, a], phase=np.pi / 2))
+        om = a * math.sqrt(2)
+    g = hb.Hermite(d, m, N, 1.0, h, dt, variant, 0, precision=prec)
+    g.set_state(u0, np.zeros((N ** d, m ** d)))
+    g.step(nsteps)
+    u, _ = g.get_state()
+    return rel_l2(u, math.cos(om * nsteps * dt) * u0)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("case", [(1, 3, 0.9, 1.0, [16, 32, 64, 128, 256]), (2, 4, 1.0, 2.0, [8, 16, 32, 64])])
+def test_split_accuracy_bar(hb, variant, case):
+    d, m, lam, T, Ns = case
+    rows = []
+    for N in Ns:
+        e64 = _standing(hb, d, m, N, lam, T, variant, hb.FP64)
+        es = _standing(hb, d, m, N, lam, T, variant, hb.SPLIT32)
+        rows.append((N, e64, es))
+        if e64 >= 1e-9:
+            assert es <= 1.2 * e64, rows
+    print(rows)
