@@ -45,7 +45,12 @@ void release(hermite_ctx *ctx) {
   for (int g = 0; g < 2; ++g) cudaFree(ctx->grid[g]);
   cudaFree(ctx->M);
   cudaFree(ctx->Mstart);
-  for (int f = 0; f < kNumForms; ++f) cudaFree(ctx->Q[f]);
+  for (int f = 0; f < kNumForms; ++f) {
+    cudaFree(ctx->Q[f]);
+    cudaFree(ctx->L[f]);
+    cudaFree(ctx->lperm[f]);
+    cudaFree(ctx->Lf[f]);
+  }
   cudaFree(ctx->par_in);
   cudaFree(ctx->staging);
   cudaFree(ctx->scratch_grid);
@@ -53,6 +58,7 @@ void release(hermite_ctx *ctx) {
   cudaFree(ctx->result);
   for (int g = 0; g < 2; ++g) cudaFree(ctx->fgrid[g]);
   cudaFree(ctx->Mc);
+  cudaFree(ctx->fscratch);
   cudaFree(ctx->outrow);
   cudaFree(ctx->npc);
 }
@@ -272,6 +278,8 @@ int hermite_create_ex(int d, int m, int64_t N, double c, double h, double dt, in
       if (!cuda_ok(ctx, cudaMemset(ctx->fgrid[g], 0, sizeof(float2) * ctx->ncoef * ctx->ld[g]), "memset"))
         rc = HERMITE_ERR_CUDA;
     if (rc == HERMITE_OK) rc = build_split_operator(ctx);
+    if (rc == HERMITE_OK) rc = build_split_forms(ctx);
+    if (cons) alloc((void **)&ctx->fscratch, sizeof(float2) * ctx->Nu * maxld, "split scratch");
   }
   if (rc == HERMITE_OK && !cuda_ok(ctx, cudaDeviceSynchronize(), "create sync")) rc = HERMITE_ERR_CUDA;
   if (rc != HERMITE_OK) {
@@ -385,10 +393,27 @@ int hermite_set_grid(hermite_ctx *ctx, int grid, const double *u, const double *
 
 int hermite_energy(hermite_ctx *ctx, double out[3]) {
   if (!ctx || !out) return ctx ? fail(ctx, HERMITE_ERR_ARG, "out is NULL") : HERMITE_ERR_ARG;
-  int rc = sync_fp64_from_split(ctx, -1);  // energies are FP64 reductions
-  if (rc) return rc;
+  int rc = HERMITE_OK;
   double host[4] = {0, 0, 0, 0};
-  if (!is_cons(ctx)) {
+  if (is_split(ctx)) {
+    // split contexts reduce their hi + lo levels in the same arithmetic
+    if (!is_cons(ctx)) {
+      const int g = newest_grid(ctx);
+      rc = launch_energy_form_split(ctx, 0, g, ctx->fgrid[g], ctx->fgrid[g], ctx->result + 0);
+      if (!rc) rc = launch_energy_form_split(ctx, 1, g, ctx->fgrid[g], ctx->fgrid[g], ctx->result + 1);
+    } else {
+      const int gnew = newest_grid(ctx), gold = 1 - gnew;
+      const size_t bytes = sizeof(float2) * ctx->Nu * ctx->ld[gold];
+      if (!cuda_ok(ctx, cudaMemcpyAsync(ctx->fscratch, ctx->fgrid[gold], bytes, cudaMemcpyDeviceToDevice,
+                                        ctx->stream),
+                   "copy level"))
+        return HERMITE_ERR_CUDA;
+      rc = launch_half_step_split_into(ctx, gold, ctx->fgrid[gnew], ctx->fscratch, true);
+      if (!rc) rc = launch_energy_form_split(ctx, 0, gnew, ctx->fgrid[gnew], ctx->fgrid[gnew], ctx->result + 0);
+      if (!rc) rc = launch_energy_form_split(ctx, 0, gold, ctx->fscratch, ctx->fgrid[gold], ctx->result + 1);
+      if (!rc) rc = launch_energy_form_split(ctx, 1, 0, ctx->fgrid[0], ctx->fgrid[0], ctx->result + 2);
+    }
+  } else if (!is_cons(ctx)) {
     const int g = newest_grid(ctx);
     rc = launch_energy_form(ctx, 0, g, ctx->grid[g], ctx->grid[g], ctx->result + 0);
     if (!rc) rc = launch_energy_form(ctx, 1, g, ctx->grid[g], ctx->grid[g], ctx->result + 1);

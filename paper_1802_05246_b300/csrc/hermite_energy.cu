@@ -114,13 +114,16 @@ __global__ void __launch_bounds__(kEThreads) energy_kernel(Geometry g, const dou
           class_value<D>(B + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
     double cell = 0.0;
     for (int b = 0; b < nq; ++b) {
+      const bool quad = (A == B);
       const double ya =
-          (A == B) ? yb[b * kEThreads + threadIdx.x]
-                   : class_value<D>(A + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
+          quad ? yb[b * kEThreads + threadIdx.x]
+               : class_value<D>(A + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
       if (ya == 0.0) continue;
       const double *qrow = Qs + (size_t)b * nq;
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int k = 0;
+      // a quadratic form needs only the upper triangle of the symmetric Q_c:
+      // y^T Q y = sum_b y_b (Q_bb y_b + 2 sum_{k>b} Q_bk y_k)
+      int k = quad ? b + 1 : 0;
       for (; k + 3 < nq; k += 4) {
         s0 = fma(qrow[k], yb[k * kEThreads + threadIdx.x], s0);
         s1 = fma(qrow[k + 1], yb[(k + 1) * kEThreads + threadIdx.x], s1);
@@ -128,13 +131,167 @@ __global__ void __launch_bounds__(kEThreads) energy_kernel(Geometry g, const dou
         s3 = fma(qrow[k + 3], yb[(k + 3) * kEThreads + threadIdx.x], s3);
       }
       for (; k < nq; ++k) s0 = fma(qrow[k], yb[k * kEThreads + threadIdx.x], s0);
-      cell = fma(ya, (s0 + s1) + (s2 + s3), cell);
+      const double off = (s0 + s1) + (s2 + s3);
+      cell = quad ? fma(ya, fma(qrow[b], ya, 2.0 * off), cell) : fma(ya, off, cell);
     }
     total = fma(w, cell, total);
   }
   red[threadIdx.x] = total;
   __syncthreads();
   for (int off = kEThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// Low-rank form Q_c = L_c^T L_c: E_cell = sum_r (L_r . y_c(A)) (L_r . y_c(B)).
+template <int D>
+__global__ void __launch_bounds__(kEThreads) energy_lowrank_kernel(Geometry g, const double *__restrict__ L,
+                                                                   int rmax, int nq,
+                                                                   const int8_t *__restrict__ par,
+                                                                   const double *__restrict__ A,
+                                                                   const double *__restrict__ B, double *partials) {
+  extern __shared__ double sm[];
+  const int c = blockIdx.y;
+  const bool quad = (A == B);
+  double *Ls = sm;                                   // [rmax][nq]
+  double *ya = Ls + (size_t)rmax * nq;               // [nq][kEThreads]
+  double *ybv = quad ? ya : ya + (size_t)nq * kEThreads;
+  int8_t *pin = reinterpret_cast<int8_t *>(ya + (size_t)(quad ? 1 : 2) * nq * kEThreads);
+  __shared__ double red[kEThreads];
+  const double *Lc = L + (size_t)c * rmax * nq;
+  for (int i = threadIdx.x; i < rmax * nq; i += kEThreads) Ls[i] = Lc[i];
+  for (int i = threadIdx.x; i < nq; i += kEThreads) pin[i] = par[i];
+  __syncthreads();
+  double total = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * kEThreads;
+  for (int64_t t = (int64_t)blockIdx.x * kEThreads + threadIdx.x; t < g.nodes_dst; t += stride) {
+    int64_t idx[1 << D];
+    int gm[1 << D];
+    double w;
+    cell_corners_e<D>(g, t, idx, gm, &w);
+    for (int b = 0; b < nq; ++b) {
+      ya[b * kEThreads + threadIdx.x] = class_value<D>(A + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
+      if (!quad)
+        ybv[b * kEThreads + threadIdx.x] =
+            class_value<D>(B + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
+    }
+    double cell = 0.0;
+    for (int r = 0; r < rmax; ++r) {
+      const double *lrow = Ls + (size_t)r * nq;
+      double sa0 = 0.0, sa1 = 0.0, sb0 = 0.0, sb1 = 0.0;
+      int k = 0;
+      for (; k + 1 < nq; k += 2) {
+        sa0 = fma(lrow[k], ya[k * kEThreads + threadIdx.x], sa0);
+        sa1 = fma(lrow[k + 1], ya[(k + 1) * kEThreads + threadIdx.x], sa1);
+        if (!quad) {
+          sb0 = fma(lrow[k], ybv[k * kEThreads + threadIdx.x], sb0);
+          sb1 = fma(lrow[k + 1], ybv[(k + 1) * kEThreads + threadIdx.x], sb1);
+        }
+      }
+      for (; k < nq; ++k) {
+        sa0 = fma(lrow[k], ya[k * kEThreads + threadIdx.x], sa0);
+        if (!quad) sb0 = fma(lrow[k], ybv[k * kEThreads + threadIdx.x], sb0);
+      }
+      const double la = sa0 + sa1;
+      cell = fma(la, quad ? la : (sb0 + sb1), cell);
+    }
+    total = fma(w, cell, total);
+  }
+  red[threadIdx.x] = total;
+  __syncthreads();
+  for (int off = kEThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// Factored form Q_c = L_c^T L_c (L_c upper triangular in a permuted column
+// order, or a short dense low-rank factor): a block takes a tile of 64 cells
+// and one class, stages their class vectors y_c (columns permuted) in shared
+// memory, and thread (cell group cg, row group rg) forms z = L_r . y for four
+// cells and rows r = rg, rg+16, ... starting at column r when L is
+// triangular.  E_cell = sum_r z_r(A) z_r(B).
+constexpr int kFTile = 64;
+constexpr int kFThreads = 256;
+
+template <int D>
+__global__ void __launch_bounds__(kFThreads) energy_factored_kernel(
+    Geometry g, const double *__restrict__ L, int lrows, int rmax, int tri, const int16_t *__restrict__ perm, int nq,
+    const int8_t *__restrict__ par, const double *__restrict__ A, const double *__restrict__ B, double *partials) {
+  constexpr int NC = 1 << D;
+  extern __shared__ double sm[];
+  const int c = blockIdx.y;
+  const bool quad = (A == B);
+  const int ld = nq | 1;  // odd row stride: conflict-free column reads
+  double *Ls = sm;                                    // [rmax][nq]
+  double *YA = Ls + (size_t)rmax * nq;                // [kFTile][ld]
+  double *YB = quad ? YA : YA + (size_t)kFTile * ld;  // [kFTile][ld]
+  double *cw = YA + (size_t)(quad ? 1 : 2) * kFTile * ld;  // [kFTile]
+  int64_t *cidx = reinterpret_cast<int64_t *>(cw + kFTile);  // [kFTile][NC]
+  int *cgm = reinterpret_cast<int *>(cidx + kFTile * NC);    // [kFTile][NC]
+  int16_t *ps = reinterpret_cast<int16_t *>(cgm + kFTile * NC);  // [nq]
+  int8_t *pin = reinterpret_cast<int8_t *>(ps + nq);             // [nq]
+  __shared__ double red[kFThreads];
+  const double *Lc = L + (size_t)c * lrows * nq;
+  for (int i = threadIdx.x; i < rmax * nq; i += kFThreads) Ls[i] = Lc[i];
+  for (int i = threadIdx.x; i < nq; i += kFThreads) {
+    ps[i] = perm[(size_t)c * nq + i];
+    pin[i] = par[i];
+  }
+  const int cg = threadIdx.x & 15, rg = threadIdx.x >> 4;
+  double total = 0.0;
+  const int64_t ntiles = (g.nodes_dst + kFTile - 1) / kFTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x < kFTile) {
+      const int64_t t = tile * kFTile + threadIdx.x;
+      if (t < g.nodes_dst) {
+        double w;
+        cell_corners_e<D>(g, t, cidx + threadIdx.x * NC, cgm + threadIdx.x * NC, &w);
+        cw[threadIdx.x] = w;
+      } else {
+        for (int s = 0; s < NC; ++s) {
+          cidx[threadIdx.x * NC + s] = 0;
+          cgm[threadIdx.x * NC + s] = 0;
+        }
+        cw[threadIdx.x] = 0.0;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kFTile * nq; e += kFThreads) {
+      // consecutive lanes take consecutive cells of one coefficient plane so
+      // that their corner gathers coalesce
+      const int i = e % kFTile, k = e / kFTile, b = ps[k];
+      YA[i * ld + k] = class_value<D>(A + (size_t)b * g.ld_src, cidx + i * NC, cgm + i * NC, g.bc, pin[b], c ^ pin[b]);
+      if (!quad)
+        YB[i * ld + k] =
+            class_value<D>(B + (size_t)b * g.ld_src, cidx + i * NC, cgm + i * NC, g.bc, pin[b], c ^ pin[b]);
+    }
+    __syncthreads();
+    double e4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int r = rg; r < rmax; r += 16) {
+      const double *lrow = Ls + (size_t)r * nq;
+      double za[4] = {0.0, 0.0, 0.0, 0.0}, zb[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = tri ? r : 0; k < nq; ++k) {
+        const double l = lrow[k];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          za[i] = fma(l, YA[(cg + 16 * i) * ld + k], za[i]);
+          if (!quad) zb[i] = fma(l, YB[(cg + 16 * i) * ld + k], zb[i]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) e4[i] = fma(za[i], quad ? za[i] : zb[i], e4[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) total = fma(cw[cg + 16 * i], e4[i], total);
+  }
+  red[threadIdx.x] = total;
+  __syncthreads();
+  for (int off = kFThreads / 2; off > 0; off >>= 1) {
     if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
     __syncthreads();
   }
@@ -172,7 +329,31 @@ int launch_energy_d(hermite_ctx *ctx, const Geometry &g, int form, const double 
   int64_t blocks = std::max<int64_t>(1, (g.nodes_dst + kEThreads - 1) / kEThreads);
   blocks = std::min<int64_t>(blocks, ctx->partials_len / nclass);
   dim3 grid((unsigned)blocks, (unsigned)nclass);
-  energy_kernel<D><<<grid, kEThreads, smem, ctx->stream>>>(g, ctx->Q[form], nq, ctx->par_in, A, B, ctx->partials);
+  if (ctx->L[form]) {
+    static thread_local int configured_f = -1;
+    if (configured_f != ctx->device) {
+      if (!cuda_ok(ctx,
+                   cudaFuncSetAttribute(energy_factored_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        220 * 1024),
+                   "cudaFuncSetAttribute energy factored"))
+        return HERMITE_ERR_CUDA;
+      configured_f = ctx->device;
+    }
+    const int rmax = ctx->rmax[form];
+    const int ld = nq | 1;
+    const size_t smem_f = sizeof(double) * ((size_t)rmax * nq + (A == B ? 1 : 2) * (size_t)kFTile * ld + kFTile) +
+                          sizeof(int64_t) * kFTile * nclass + sizeof(int) * kFTile * nclass + 3 * nq + 16;
+    int64_t fblocks = std::max<int64_t>(1, (g.nodes_dst + kFTile - 1) / kFTile);
+    fblocks = std::min<int64_t>(fblocks, ctx->partials_len / nclass);
+    dim3 fgrid((unsigned)fblocks, (unsigned)nclass);
+    energy_factored_kernel<D><<<fgrid, kFThreads, smem_f, ctx->stream>>>(
+        g, ctx->L[form], ctx->lrows[form], rmax, ctx->ltri[form], ctx->lperm[form], nq, ctx->par_in, A, B,
+        ctx->partials);
+    reduce_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, fblocks * nclass, ctx->formscale[form], result_slot);
+    return cuda_ok(ctx, cudaGetLastError(), "energy_factored_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+  } else {
+    energy_kernel<D><<<grid, kEThreads, smem, ctx->stream>>>(g, ctx->Q[form], nq, ctx->par_in, A, B, ctx->partials);
+  }
   reduce_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, blocks * nclass, ctx->formscale[form], result_slot);
   return cuda_ok(ctx, cudaGetLastError(), "energy_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }

@@ -44,6 +44,13 @@ struct hermite_ctx {
   double *Mstart = nullptr;                // conservative start-up [Nu][Nu+Nv]
   double *Q[hermite::kNumForms] = {nullptr, nullptr};  // energy forms [2^d][nq][nq]
   int nq[hermite::kNumForms] = {0, 0};
+  // low-rank factors of the forms whose integrands span few monomials per
+  // parity class: Q_c = L_c^T L_c, L stored [2^d][rmax][nq] (zero-padded rows)
+  double *L[hermite::kNumForms] = {nullptr, nullptr};
+  int rmax[hermite::kNumForms] = {0, 0};   // rows used per class
+  int lrows[hermite::kNumForms] = {0, 0};  // rows allocated per class
+  int ltri[hermite::kNumForms] = {0, 0};   // 1: pivoted Cholesky (triangular after permutation)
+  int16_t *lperm[hermite::kNumForms] = {nullptr, nullptr};  // [2^d][nq] column order
   double formscale[hermite::kNumForms] = {0, 0};
   int8_t *par_in = nullptr;    // parity bits of each operator input coefficient
   int8_t *par_out = nullptr;   // parity bits of each operator output coefficient
@@ -60,6 +67,8 @@ struct hermite_ctx {
   int precision = 0;
   float2 *fgrid[2] = {nullptr, nullptr};  // SoA [ncoef][ld] of (hi, lo)
   float2 *Mc = nullptr;        // operator rows grouped by output parity class
+  float2 *Lf[hermite::kNumForms] = {nullptr, nullptr};  // energy factors split hi + lo
+  float2 *fscratch = nullptr;  // one split grid (conservative energy)
   int16_t *outrow = nullptr;   // [2^d][nomax] output row of each class slot (-1 unused)
   int8_t *npc = nullptr;       // outputs per class
   int nomax = 0;
@@ -87,6 +96,10 @@ int build_split_operator(hermite_ctx *ctx);
 int launch_half_step_split(hermite_ctx *ctx, int dst, bool subtract_old);
 int split_from_fp64(hermite_ctx *ctx, int grid);
 int split_to_fp64(hermite_ctx *ctx, int grid);
+int build_split_forms(hermite_ctx *ctx);
+int launch_energy_form_split(hermite_ctx *ctx, int form, int grid, const float2 *A, const float2 *B,
+                             double *result_slot);
+int launch_half_step_split_into(hermite_ctx *ctx, int dst, const float2 *src, float2 *out, bool subtract_old);
 
 // Energy reduction (hermite_energy.cu).
 int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const double *B,

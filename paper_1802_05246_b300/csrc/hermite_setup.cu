@@ -345,6 +345,92 @@ __global__ void form_components_kernel(FormParams p) {
   }
 }
 
+// Cholesky factor (upper, G = R^T R) of the 1-D monomial Gram matrix
+// G[a][b] = int_{-1/2}^{1/2} xi^{a+b} dxi, a, b < E.  Its zero pattern follows
+// the parity of a + b, so odd and even exponents stay separate.
+__global__ void gram_cholesky_kernel(int E, double *R) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < E * E; ++i) R[i] = 0.0;
+  for (int j = 0; j < E; ++j) {
+    double s = moment(2 * j);
+    for (int k = 0; k < j; ++k) s -= R[k * E + j] * R[k * E + j];
+    const double rjj = sqrt(s);
+    R[j * E + j] = rjj;
+    for (int i = j + 1; i < E; ++i) {
+      double t = moment(i + j);
+      for (int k = 0; k < j; ++k) t -= R[k * E + j] * R[k * E + i];
+      R[j * E + i] = t / rjj;
+    }
+  }
+}
+
+// RF = (R x ... x R) F for every component polynomial: |RF|^2 = int F^2
+__global__ void form_cholesky_apply_kernel(const double *F, int64_t npoly, int d, int E, int B, const double *R,
+                                           double *RF, double *work) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= npoly) return;
+  const double *f = F + id * B;
+  double *out = RF + id * B, *tmp = work + id * B;
+  for (int k = 0; k < B; ++k) out[k] = f[k];
+  for (int ax = 0; ax < d; ++ax) {
+    for (int k = 0; k < B; ++k) {
+      int a[kMaxDim];
+      unravel(d, E, k, a);
+      const int row = a[ax];
+      double acc = 0.0;
+      for (int b = row; b < E; ++b) {
+        a[ax] = b;
+        acc += R[row * E + b] * out[ravel(d, E, a)];
+      }
+      tmp[k] = acc;
+    }
+    for (int k = 0; k < B; ++k) out[k] = tmp[k];
+  }
+}
+
+// Pivoted Cholesky of each class matrix Q_c (symmetric positive semidefinite):
+// Q_c[perm][perm] = L^T L with L upper triangular in the permuted order, rows
+// beyond the numerical rank dropped (remaining diagonal <= 1e-15 of the
+// largest).  One thread per class.  L_out[c][r][k] holds row r against the
+// permuted column k; perm_out[c][k] is the original column.
+__global__ void pivoted_cholesky_kernel(const double *Q, int nclass, int nq, double *work, double *L_out,
+                                        int16_t *perm_out, int *rank_out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nclass) return;
+  double *A = work + (size_t)c * nq * nq;
+  for (int i = 0; i < nq * nq; ++i) A[i] = Q[(size_t)c * nq * nq + i];
+  int16_t *perm = perm_out + (size_t)c * nq;
+  double *L = L_out + (size_t)c * nq * nq;
+  for (int i = 0; i < nq; ++i) perm[i] = (int16_t)i;
+  for (int i = 0; i < nq * nq; ++i) L[i] = 0.0;
+  double dmax0 = 0.0;
+  for (int i = 0; i < nq; ++i) dmax0 = fmax(dmax0, A[i * nq + i]);
+  int r = 0;
+  for (; r < nq; ++r) {
+    // pivot: largest remaining diagonal
+    int p = r;
+    for (int i = r + 1; i < nq; ++i)
+      if (A[perm[i] * nq + perm[i]] > A[perm[p] * nq + perm[p]]) p = i;
+    const int16_t tp = perm[r];
+    perm[r] = perm[p];
+    perm[p] = tp;
+    for (int k = 0; k < r; ++k) {  // keep earlier rows aligned with the permuted columns
+      const double t = L[k * nq + r];
+      L[k * nq + r] = L[k * nq + p];
+      L[k * nq + p] = t;
+    }
+    const double piv = A[perm[r] * nq + perm[r]];
+    if (!(piv > 1e-15 * dmax0)) break;
+    const double lrr = sqrt(piv);
+    L[r * nq + r] = lrr;
+    for (int j = r + 1; j < nq; ++j) L[r * nq + j] = A[perm[r] * nq + perm[j]] / lrr;
+    // Schur complement on the remaining (original-index) entries
+    for (int i = r + 1; i < nq; ++i)
+      for (int j = r + 1; j < nq; ++j) A[perm[i] * nq + perm[j]] -= L[r * nq + i] * L[r * nq + j];
+  }
+  rank_out[c] = r;
+}
+
 __global__ void form_gram_kernel(const double *F, const double *HF, int nclass, int nq, int ncomp,
                                  int B, double *Q) {
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -383,6 +469,107 @@ int make_basis(hermite_ctx *ctx, Basis &bs) {
 void free_basis(Basis &bs) {
   cudaFree(bs.Hm);
   cudaFree(bs.Hm1);
+}
+
+// Factor of a form with many monomials per class: pivoted Cholesky of Q_c.
+int build_cholesky_factor(hermite_ctx *ctx, int f, int nclass, int nq) {
+  double *work = nullptr;
+  int *rank = nullptr;
+  int rc = HERMITE_OK;
+  const size_t n2 = (size_t)nclass * nq * nq;
+  if (!cuda_ok(ctx, cudaMalloc(&work, sizeof(double) * n2), "cudaMalloc chol work") ||
+      !cuda_ok(ctx, cudaMalloc(&rank, sizeof(int) * nclass), "cudaMalloc rank") ||
+      !cuda_ok(ctx, cudaMalloc(&ctx->L[f], sizeof(double) * n2), "cudaMalloc L") ||
+      !cuda_ok(ctx, cudaMalloc(&ctx->lperm[f], sizeof(int16_t) * nclass * nq), "cudaMalloc perm")) {
+    rc = HERMITE_ERR_ALLOC;
+  } else {
+    pivoted_cholesky_kernel<<<1, 32, 0, ctx->stream>>>(ctx->Q[f], nclass, nq, work, ctx->L[f], ctx->lperm[f], rank);
+    std::vector<int> rh(nclass);
+    if (!cuda_ok(ctx, cudaGetLastError(), "pivoted_cholesky_kernel") ||
+        !cuda_ok(ctx, cudaMemcpyAsync(rh.data(), rank, sizeof(int) * nclass, cudaMemcpyDeviceToHost, ctx->stream),
+                 "rank copy") ||
+        !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "cholesky sync")) {
+      rc = HERMITE_ERR_CUDA;
+    } else {
+      int rmax = 0;
+      for (int c = 0; c < nclass; ++c) rmax = std::max(rmax, rh[c]);
+      ctx->rmax[f] = rmax;
+      ctx->lrows[f] = nq;
+      ctx->ltri[f] = 1;
+    }
+  }
+  cudaFree(work);
+  cudaFree(rank);
+  return rc;
+}
+
+// Low-rank factor of a form: rows (component k, monomial mu) of
+// (R x .. x R) F_{c,beta,k} that are non-zero for some input beta.  Kept only
+// when every class has at most nq/2 rows (then r*nq < nq^2/2 multiply-adds).
+int build_lowrank_factor(hermite_ctx *ctx, int f, const double *F, int nclass, int nq, int ncomp,
+                         const PolySpace &P) {
+  const int64_t npoly = (int64_t)nclass * nq * ncomp;
+  const size_t nF = (size_t)npoly * P.B;
+  double *R = nullptr, *RF = nullptr, *work = nullptr;
+  int rc = HERMITE_OK;
+  if (!cuda_ok(ctx, cudaMalloc(&R, sizeof(double) * P.E * P.E), "cudaMalloc R") ||
+      !cuda_ok(ctx, cudaMalloc(&RF, sizeof(double) * nF), "cudaMalloc RF") ||
+      !cuda_ok(ctx, cudaMalloc(&work, sizeof(double) * nF), "cudaMalloc work")) {
+    rc = HERMITE_ERR_ALLOC;
+  } else {
+    gram_cholesky_kernel<<<1, 1, 0, ctx->stream>>>(P.E, R);
+    form_cholesky_apply_kernel<<<(unsigned)((npoly + 63) / 64), 64, 0, ctx->stream>>>(F, npoly, P.d, P.E, P.B, R,
+                                                                                       RF, work);
+    std::vector<double> h(nF);
+    if (!cuda_ok(ctx, cudaGetLastError(), "cholesky kernels") ||
+        !cuda_ok(ctx, cudaMemcpyAsync(h.data(), RF, sizeof(double) * nF, cudaMemcpyDeviceToHost, ctx->stream),
+                 "RF copy") ||
+        !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "RF sync")) {
+      rc = HERMITE_ERR_CUDA;
+    } else {
+      // support rows per class
+      std::vector<std::vector<std::pair<int, int>>> rows(nclass);
+      int rmax = 0;
+      for (int c = 0; c < nclass; ++c) {
+        for (int k = 0; k < ncomp; ++k)
+          for (int mu = 0; mu < P.B; ++mu) {
+            bool nz = false;
+            for (int b = 0; b < nq && !nz; ++b) nz = h[(((size_t)c * nq + b) * ncomp + k) * P.B + mu] != 0.0;
+            if (nz) rows[c].push_back({k, mu});
+          }
+        rmax = std::max<int>(rmax, (int)rows[c].size());
+      }
+      if (2 * rmax <= nq) {
+        std::vector<double> Lh((size_t)nclass * rmax * nq, 0.0);
+        for (int c = 0; c < nclass; ++c)
+          for (size_t r = 0; r < rows[c].size(); ++r)
+            for (int b = 0; b < nq; ++b)
+              Lh[((size_t)c * rmax + r) * nq + b] =
+                  h[(((size_t)c * nq + b) * ncomp + rows[c][r].first) * P.B + rows[c][r].second];
+        std::vector<int16_t> ident((size_t)nclass * nq);
+        for (size_t i = 0; i < ident.size(); ++i) ident[i] = (int16_t)(i % nq);
+        if (!cuda_ok(ctx, cudaMalloc(&ctx->L[f], sizeof(double) * Lh.size()), "cudaMalloc L") ||
+            !cuda_ok(ctx, cudaMalloc(&ctx->lperm[f], sizeof(int16_t) * ident.size()), "cudaMalloc perm")) {
+          rc = HERMITE_ERR_ALLOC;
+        } else if (!cuda_ok(ctx, cudaMemcpy(ctx->L[f], Lh.data(), sizeof(double) * Lh.size(), cudaMemcpyHostToDevice),
+                            "L copy") ||
+                   !cuda_ok(ctx, cudaMemcpy(ctx->lperm[f], ident.data(), sizeof(int16_t) * ident.size(),
+                                            cudaMemcpyHostToDevice),
+                            "perm copy")) {
+          rc = HERMITE_ERR_CUDA;
+        } else {
+          ctx->rmax[f] = rmax;
+          ctx->lrows[f] = rmax;
+          ctx->ltri[f] = 0;
+        }
+      }
+    }
+  }
+  cudaFree(R);
+  cudaFree(RF);
+  cudaFree(work);
+  if (rc == HERMITE_OK && !ctx->L[f]) rc = build_cholesky_factor(ctx, f, nclass, nq);
+  return rc;
 }
 
 PolySpace make_space(const hermite_ctx *ctx, const Basis &bs) {
@@ -483,6 +670,7 @@ int build_energy_forms(hermite_ctx *ctx) {
         ctx->formscale[f] = c2 * hd * pow(ctx->h, -2.0 * (d * m + 1));
       else
         ctx->formscale[f] = hd * pow(ctx->h, -2.0 * d * (m + 1));
+      if (rc == HERMITE_OK) rc = build_lowrank_factor(ctx, f, F, nclass, nq, ncomp, P);
     }
     cudaFree(F);
     cudaFree(HF);

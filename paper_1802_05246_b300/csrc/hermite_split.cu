@@ -236,6 +236,174 @@ int launch_split_d(hermite_ctx *ctx, const Geometry &g, const float2 *src, float
   return launch_split_dn<D, 32>(ctx, g, src, dst, sub);
 }
 
+// Energy forms on split-precision levels: the factored form of the FP64
+// kernel (Q_c = L_c^T L_c, tile of 64 cells per block, class vectors staged in
+// shared memory) with the class vectors, the factor and every product in
+// hi + lo arithmetic; block partial sums are returned as FP64 hi + lo.
+constexpr int kSFTile = 64;
+constexpr int kSFThreads = 256;
+
+template <int D>
+__global__ void __launch_bounds__(kSFThreads) energy_factored_split_kernel(
+    Geometry g, const float2 *__restrict__ L, int lrows, int rmax, int tri, const int16_t *__restrict__ perm, int nq,
+    const int8_t *__restrict__ par, const float2 *__restrict__ A, const float2 *__restrict__ B, double *partials) {
+  constexpr int NC = 1 << D;
+  extern __shared__ float2 smf[];
+  const int c = blockIdx.y;
+  const bool quad = (A == B);
+  const int ld = nq | 1;
+  float2 *Ls = smf;                                    // [rmax][nq]
+  float2 *YA = Ls + (size_t)rmax * nq;                 // [kSFTile][ld]
+  float2 *YB = quad ? YA : YA + (size_t)kSFTile * ld;
+  double *cw = reinterpret_cast<double *>(YA + (size_t)(quad ? 1 : 2) * kSFTile * ld);  // [kSFTile]
+  int64_t *cidx = reinterpret_cast<int64_t *>(cw + kSFTile);
+  int *cgm = reinterpret_cast<int *>(cidx + kSFTile * NC);
+  int16_t *ps = reinterpret_cast<int16_t *>(cgm + kSFTile * NC);
+  int8_t *pin = reinterpret_cast<int8_t *>(ps + nq);
+  __shared__ double red[kSFThreads];
+  const float2 *Lc = L + (size_t)c * lrows * nq;
+  for (int i = threadIdx.x; i < rmax * nq; i += kSFThreads) Ls[i] = Lc[i];
+  for (int i = threadIdx.x; i < nq; i += kSFThreads) {
+    ps[i] = perm[(size_t)c * nq + i];
+    pin[i] = par[i];
+  }
+  const int cg = threadIdx.x & 15, rg = threadIdx.x >> 4;
+  float2 total = make_float2(0.f, 0.f);
+  const int64_t ntiles = (g.nodes_dst + kSFTile - 1) / kSFTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x < kSFTile) {
+      const int64_t t = tile * kSFTile + threadIdx.x;
+      double w = 0.0;
+      if (t < g.nodes_dst) {
+        corners_split<D>(g, t, cidx + threadIdx.x * NC, cgm + threadIdx.x * NC);
+        int64_t r = t;
+        w = 1.0;
+        for (int i = D - 1; i >= 0; --i) {
+          const int64_t ti = r % g.n_dst;
+          r /= g.n_dst;
+          // a cell centred on a boundary primal node is cut in half by the boundary
+          if (g.bc != HERMITE_PERIODIC && g.dst == 0 && (ti == 0 || ti == g.n_dst - 1)) w *= 0.5;
+        }
+      } else {
+        for (int s = 0; s < NC; ++s) {
+          cidx[threadIdx.x * NC + s] = 0;
+          cgm[threadIdx.x * NC + s] = 0;
+        }
+      }
+      cw[threadIdx.x] = w;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSFTile * nq; e += kSFThreads) {
+      // consecutive lanes take consecutive cells of one coefficient plane so
+      // that their corner gathers coalesce
+      const int i = e % kSFTile, k = e / kSFTile, b = ps[k], q = c ^ pin[b];
+      const int64_t *idx = cidx + i * NC;
+      const int *gm = cgm + i * NC;
+      float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const bool neg = ((__popc(q & s) & 1) != 0) != (gm[s] && ghost_negates(g.bc, gm[s], pin[b]));
+        float2 v = A[(size_t)b * g.ld_src + idx[s]];
+        ya = df_add(ya, neg ? df_neg(v) : v);
+        if (!quad) {
+          v = B[(size_t)b * g.ld_src + idx[s]];
+          yb = df_add(yb, neg ? df_neg(v) : v);
+        }
+      }
+      YA[i * ld + k] = df_norm(ya);
+      if (!quad) YB[i * ld + k] = df_norm(yb);
+    }
+    __syncthreads();
+    float2 e4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) e4[i] = make_float2(0.f, 0.f);
+    for (int r = rg; r < rmax; r += 16) {
+      const float2 *lrow = Ls + (size_t)r * nq;
+      float2 za[4], zb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        za[i] = make_float2(0.f, 0.f);
+        zb[i] = make_float2(0.f, 0.f);
+      }
+      for (int k = tri ? r : 0; k < nq; ++k) {
+        const float2 l = lrow[k];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          df_fma(za[i], l, YA[(cg + 16 * i) * ld + k]);
+          if (!quad) df_fma(zb[i], l, YB[(cg + 16 * i) * ld + k]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 a = df_norm(za[i]);
+        df_fma(e4[i], a, quad ? a : df_norm(zb[i]));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      // weights are 1, 1/2, 1/4 or 1/8: exact in FP32
+      const float w = (float)cw[cg + 16 * i];
+      const float2 e = df_norm(e4[i]);
+      total = df_add(total, make_float2(w * e.x, w * e.y));
+    }
+  }
+  red[threadIdx.x] = (double)total.x + (double)total.y;
+  __syncthreads();
+  for (int off = kSFThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void split_factor_kernel(const double *L, int64_t n, float2 *Lf) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = L[i];
+    const float hi = __double2float_rn(x);
+    Lf[i] = make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+}
+
+__global__ void reduce_partials_kernel(const double *partials, int64_t n, double scale, double *out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) acc += partials[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = scale * red[0];
+}
+
+template <int D>
+int launch_energy_split_d(hermite_ctx *ctx, int form, int grid, const float2 *A, const float2 *B, double *out) {
+  const Geometry g = make_geometry(ctx, 1 - grid);
+  const int nclass = 1 << D, nq = ctx->nq[form], rmax = ctx->rmax[form], ld = nq | 1;
+  static thread_local int configured = -1;
+  if (configured != ctx->device) {
+    if (!cuda_ok(ctx,
+                 cudaFuncSetAttribute(energy_factored_split_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      220 * 1024),
+                 "cudaFuncSetAttribute split energy"))
+      return HERMITE_ERR_CUDA;
+    configured = ctx->device;
+  }
+  const size_t smem = sizeof(float2) * ((size_t)rmax * nq + (A == B ? 1 : 2) * (size_t)kSFTile * ld) +
+                      sizeof(double) * kSFTile + sizeof(int64_t) * kSFTile * nclass + sizeof(int) * kSFTile * nclass +
+                      3 * nq + 16;
+  int64_t blocks = std::max<int64_t>(1, (g.nodes_dst + kSFTile - 1) / kSFTile);
+  blocks = std::min<int64_t>(blocks, ctx->partials_len / nclass);
+  dim3 grd((unsigned)blocks, (unsigned)nclass);
+  energy_factored_split_kernel<D><<<grd, kSFThreads, smem, ctx->stream>>>(
+      g, ctx->Lf[form], ctx->lrows[form], rmax, ctx->ltri[form], ctx->lperm[form], nq, ctx->par_in, A, B,
+      ctx->partials);
+  reduce_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, blocks * nclass, ctx->formscale[form], out);
+  return cuda_ok(ctx, cudaGetLastError(), "energy_factored_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
 // operator rows grouped by output parity class, each entry split hi + lo
 __global__ void split_operator_kernel(const double *M, int nci, const int16_t *outrow, int nclass, int nomax,
                                       float2 *Mc) {
@@ -306,6 +474,36 @@ int build_split_operator(hermite_ctx *ctx) {
       !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "split operator sync"))
     return HERMITE_ERR_CUDA;
   return HERMITE_OK;
+}
+
+int build_split_forms(hermite_ctx *ctx) {
+  for (int f = 0; f < kNumForms; ++f) {
+    const int64_t n = (int64_t)(1 << ctx->d) * ctx->lrows[f] * ctx->nq[f];
+    if (!cuda_ok(ctx, cudaMalloc(&ctx->Lf[f], sizeof(float2) * std::max<int64_t>(n, 1)), "cudaMalloc Lf"))
+      return HERMITE_ERR_ALLOC;
+    split_factor_kernel<<<64, 256, 0, ctx->stream>>>(ctx->L[f], n, ctx->Lf[f]);
+  }
+  return cuda_ok(ctx, cudaGetLastError(), "split_factor_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+int launch_energy_form_split(hermite_ctx *ctx, int form, int grid, const float2 *A, const float2 *B,
+                             double *result_slot) {
+  switch (ctx->d) {
+    case 1: return launch_energy_split_d<1>(ctx, form, grid, A, B, result_slot);
+    case 2: return launch_energy_split_d<2>(ctx, form, grid, A, B, result_slot);
+    case 3: return launch_energy_split_d<3>(ctx, form, grid, A, B, result_slot);
+  }
+  return HERMITE_ERR_ARG;
+}
+
+int launch_half_step_split_into(hermite_ctx *ctx, int dst, const float2 *src, float2 *out, bool subtract_old) {
+  const Geometry g = make_geometry(ctx, dst);
+  switch (ctx->d) {
+    case 1: return launch_split_d<1>(ctx, g, src, out, subtract_old);
+    case 2: return launch_split_d<2>(ctx, g, src, out, subtract_old);
+    case 3: return launch_split_d<3>(ctx, g, src, out, subtract_old);
+  }
+  return HERMITE_ERR_ARG;
 }
 
 int launch_half_step_split(hermite_ctx *ctx, int dst, bool subtract_old) {

@@ -94,3 +94,21 @@ def test_split_accuracy_bar(hb, variant, case):
         if e64 >= 1e-9:
             assert es <= 1.2 * e64, rows
     print(rows)
+
+
+@pytest.mark.parametrize("d,m,N,bc", [(3, 2, 6, 0), (2, 3, 8, 0), (1, 3, 12, 1)])
+def test_split_energies_conservative_and_boundaries(hb, d, m, N, bc):
+    """Split-precision energies (reduced in hi + lo arithmetic) agree with the
+    FP64 context's, for the conservative invariant G and non-periodic cells."""
+    h = 1.0 / N
+    rng = np.random.default_rng(5)
+    for variant in (0, 1):
+        outs = []
+        for prec in (hb.FP64, hb.SPLIT32):
+            g = hb.Hermite(d, m, N, 1.0, h, 0.9 * h, variant, bc, precision=prec)
+            n0 = g.nodes(0)
+            r = np.random.default_rng(5)
+            g.set_state(r.standard_normal((n0, g.Nu)), r.standard_normal((n0, g.Nv)))
+            g.advance_half(3)
+            outs.append(g.energy())
+        np.testing.assert_allclose(outs[1][:2], outs[0][:2], rtol=1e-10)
