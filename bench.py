@@ -4,11 +4,15 @@ Workload (the 3-D grid the throughput target is quoted on): periodic [0,1]^3,
 m = 3, N = 128 cells per axis (2,097,152 nodes, 64 u + 27 v coefficients per
 node), c dt/h = 0.9, u0 = sum of 8 Gaussian pulses (centres U[0,1)^3, widths
 U[0.05,0.1], amplitudes N(0,1), numpy PCG64 seed 0), v0 = 0, dissipative
-"full" variant, FP64.
+"full" variant, split precision (headline) and FP64.
 
 One benchmark step = one pass of the whole hot path: 8 full time steps
 (16 fused half-step launches) followed by one energy reduction (the energy
-is a diagnostic taken every 8 steps).  One DOF-update = one stored scaled
+is a diagnostic taken every 8 steps).  Both arithmetic paths run the same
+steps from the same state: `value` is the split-precision path (FP32 hi+lo,
+within 1.2x of the FP64 error wherever that error is >= 1e-9, see the tests),
+and the FP64 path is reported beside it with the difference of the two
+states after the same steps.  One DOF-update = one stored scaled
 coefficient of one node written by one half-step.  The 3 GB state is far
 larger than the 126 MB L2, so no flush is needed between steps.
 
@@ -58,6 +62,9 @@ def peaks():
 
 FP64_NOMINAL_GFLOPS = 148 * 2 * 2 * 2032e6 / 1e9  # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
 TRAFFIC_PER_LAUNCH = 379.8e6 * 8  # bytes, see profiles/half_step_f64_3d_m3.md
+SPLIT_TRAFFIC_PER_LAUNCH = 362.4e6 * 8  # bytes, see profiles/half_step_split_3d_m3.md
+FP32_NOMINAL_TOPS = 148 * 128 * 2032e6 / 1e12  # FP32 operations per second, nominal
+SPLIT_OPS_PER_NODE = (NU + NV) * (NU + NV) * 12 + (NU + NV) * D * (1 << D) * 8
 
 
 def dist_env():
@@ -170,29 +177,17 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
-    import torch
-
-    import paper_1802_05246_b300 as hb
-
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+def measure(hb, torch, dev, u0, v0, precision, args, ws, want_clocks):
+    """Time W warm-up and K benchmark steps of one context; returns a dict."""
     h = 1.0 / N
-    u0, v0 = initial_state()
-    g = hb.Hermite(D, M, N, 1.0, h, LAM * h, hb.DISSIPATIVE, hb.PERIODIC)
+    g = hb.Hermite(D, M, N, 1.0, h, LAM * h, hb.DISSIPATIVE, hb.PERIODIC, precision=precision)
     stream = torch.cuda.Stream(device=dev)
     g.set_stream(stream)
     du = torch.from_numpy(u0).to(dev)
     dv = torch.from_numpy(v0).to(dev)
     torch.cuda.synchronize()
     g.set_state_device(du, dv)
-
-    launches_per_step = 2 * FULL_STEPS_PER_STEP + 4  # 16 half-steps + 2 x (energy + reduce)
+    del du, dv
 
     def one_step(events=None):
         for _ in range(2 * FULL_STEPS_PER_STEP):
@@ -210,7 +205,8 @@ def run_ours(args):
         torch.distributed.barrier()
     half_events = []
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    clk = ClockSampler(dev.index)
+    with clk:
         torch.cuda.synchronize()
         start.record(stream)
         for _ in range(args.steps):
@@ -229,11 +225,42 @@ def run_ours(args):
         torch.distributed.barrier()
     halfs = [a.elapsed_time(b) for evs in half_events for a, b in zip(evs[:-1], evs[1:])]
     half_ms = sum(halfs) / len(halfs)
+    state = g.get_state()
+    return {"g": g, "ms": ms, "half_ms": half_ms, "energy": energy, "state": state, "one_step": one_step,
+            "clocks": clk.summary() if want_clocks else None}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1802_05246_b300 as hb
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    u0, v0 = initial_state()
+
+    fp64 = measure(hb, torch, dev, u0, v0, hb.FP64, args, ws, False)
+    split = measure(hb, torch, dev, u0, v0, hb.SPLIT32, args, ws, True)
+    fp64["g"].close()
+    # same start, same number of steps: difference of the two arithmetic paths
+    a = np.concatenate([fp64["state"][0], fp64["state"][1]], 1)
+    b = np.concatenate([split["state"][0], split["state"][1]], 1)
+    split_vs_fp64 = float(np.linalg.norm(a - b) / np.linalg.norm(a))
+    del a, b
+
     dof_per_step = 2 * FULL_STEPS_PER_STEP * DOF_PER_HALF
-    value = ws * dof_per_step * args.steps / (ms / 1e3)
+    value = ws * dof_per_step * args.steps / (split["ms"] / 1e3)
+    value64 = ws * dof_per_step * args.steps / (fp64["ms"] / 1e3)
 
     # end to end through the public API with host buffers: H2D of the state,
     # the step, and D2H of the state and the energy
+    g = split["g"]
+    one_step = split["one_step"]
     hu = torch.from_numpy(u0).pin_memory()
     hv = torch.from_numpy(v0).pin_memory()
     ou = torch.empty_like(hu).pin_memory()
@@ -251,43 +278,57 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_value = ws * dof_per_step / e2e_s
     state_bytes = NODES * (NU + NV) * 8
+    g.close()
 
     if rank != 0:
-        g.close()
         return 0
     pk = peaks()
-    flops_per_launch = NODES * FLOP_PER_NODE
-    achieved = flops_per_launch / (half_ms / 1e3) / 1e12
+    # split half-step: FP32-pipe operations of the compensated algorithm per node
+    # (one operator row per output: nci*nco multiply-adds of 12 FP32 ops each,
+    # plus the corner transform: nci*d*2^d additions of 8 FP32 ops each)
+    ops_per_launch = NODES * SPLIT_OPS_PER_NODE
+    achieved = ops_per_launch / (split["half_ms"] / 1e3) / 1e12
+    flops64 = NODES * FLOP_PER_NODE
+    achieved64 = flops64 / (fp64["half_ms"] / 1e3) / 1e12
     cpu_v, cpu_s = cpu_baseline_sample(u0, v0, 4096) if ws == 1 else (None, None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": split["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
         "config": {"workload": WORKLOAD, "d": D, "m": M, "N": N, "cfl": LAM, "variant": "dissipative",
-                   "bc": "periodic", "step": "8 full time steps (16 half-steps) + 1 energy reduction",
+                   "bc": "periodic", "precision": "split: FP32 hi+lo state and operator, three split products, "
+                                                  "compensated sums (HERMITE_SPLIT32)",
+                   "step": "8 full time steps (16 half-steps) + 1 energy reduction",
                    "l2": "inputs larger than L2 (3.05 GB read+written per half-step vs 126 MB)",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "alu", "kernel": "half_step_f64_kernel<3,96>", "achieved": achieved,
-                     "peak": FP64_NOMINAL_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": achieved / (FP64_NOMINAL_GFLOPS / 1e3),
-                     "peak_source": "FP64 nominal from unit counts and clocks (148 SMs x 2 DFMA/clk x 2032 MHz); "
-                                    "MEASURED_PEAKS.json has no FP64 entry",
-                     "flop_per_launch": flops_per_launch, "launch_ms": half_ms,
-                     "hbm_GBps_equiv": 2 * DOF_PER_HALF * 8 / (half_ms / 1e3) / 1e9,
+        "roofline": {"bound": "alu", "kernel": "half_step_split_kernel<3,16>", "achieved": achieved,
+                     "peak": FP32_NOMINAL_TOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_NOMINAL_TOPS,
+                     "peak_source": "FP32 pipe nominal (148 SMs x 128 lanes x 2.032 GHz, operations/s); "
+                                    "MEASURED_PEAKS.json has no FP32 entry",
+                     "ops_per_launch": ops_per_launch, "launch_ms": split["half_ms"],
+                     "hbm_GBps_equiv": 2 * DOF_PER_HALF * 8 / (split["half_ms"] / 1e3) / 1e9,
                      "hbm_peak_GBps": pk.get("hbm_gbs"),
-                     # dram read+write bytes of one launch from an ncu capture of the
-                     # same kernel at 64^3 (379.8 MB), scaled by the node count (x8)
-                     "traffic": TRAFFIC_PER_LAUNCH},
+                     # dram read+write per launch from an ncu capture of the same kernel at
+                     # 64^3 (scaled by the node count)
+                     "traffic": SPLIT_TRAFFIC_PER_LAUNCH},
+        "fp64": {"value": value64, "ms_per_step": fp64["ms"] / args.steps, "dtype": "f64",
+                 "roofline": {"bound": "alu", "kernel": "half_step_f64_kernel<3,96>", "achieved": achieved64,
+                              "peak": FP64_NOMINAL_GFLOPS / 1e3, "unit": "TFLOP/s",
+                              "frac": achieved64 / (FP64_NOMINAL_GFLOPS / 1e3), "launch_ms": fp64["half_ms"],
+                              "traffic": TRAFFIC_PER_LAUNCH},
+                 "energy_last": [float(x) for x in fp64["energy"]]},
+        "split_vs_fp64_rel_l2": split_vs_fp64,
         "cpu_baseline": ({"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                           "sample": f"4096 random dual nodes of the same grid, one half-step ({cpu_s:.1f} s)"}
                          if cpu_v else None),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes + 24},
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk.summary(),
-        "energy_last": [float(x) for x in energy],
+        "gpu_launches": (2 * FULL_STEPS_PER_STEP + 4) * args.steps,
+        "clocks": split["clocks"],
+        "energy_last": [float(x) for x in split["energy"]],
     }
     print(json.dumps(line), flush=True)
-    g.close()
     return 0
 
 

@@ -135,19 +135,24 @@ __global__ void __launch_bounds__(32 << D) half_step_split_kernel(
         gm[s] = 0;
       }
     }
-    // phase A for one chunk: warp w transforms coefficient b0 + w into buffer Y
-    auto transform = [&](int b0, float2 *Y) {
+    // phase A is split in two so that corner loads run ahead: load() fetches
+    // coefficient b0 + w of the chunk into registers, transform() applies the
+    // ghost signs and the corner transform and writes the class components
+    float2 x[NC];
+    auto load = [&](int b0) {
       const int b = b0 + w;
       if (b >= nci) return;
       const float2 *plane = src + (size_t)b * g.ld_src;
-      const int pb = pin[b];
-      float2 x[NC];
 #pragma unroll
-      for (int s = 0; s < NC; ++s) {
-        float2 v = plane[idx[s]];
-        if (gm[s] && ghost_negates(g.bc, gm[s], pb)) v = df_neg(v);
-        x[s] = v;
-      }
+      for (int s = 0; s < NC; ++s) x[s] = plane[idx[s]];
+    };
+    auto transform = [&](int b0, float2 *Y) {
+      const int b = b0 + w;
+      if (b >= nci) return;
+      const int pb = pin[b];
+#pragma unroll
+      for (int s = 0; s < NC; ++s)
+        if (gm[s] && ghost_negates(g.bc, gm[s], pb)) x[s] = df_neg(x[s]);
 #pragma unroll
       for (int bm = 1; bm < NC; bm <<= 1)
 #pragma unroll
@@ -163,12 +168,11 @@ __global__ void __launch_bounds__(32 << D) half_step_split_kernel(
     float2 acc[NOMAX];
 #pragma unroll
     for (int j = 0; j < NOMAX; ++j) acc[j] = make_float2(0.f, 0.f);
+    load(0);
     transform(0, Ybuf);
+    if (nchunks > 1) load(NC);
     __syncthreads();
     for (int ch = 0; ch < nchunks; ++ch) {
-      // the next chunk is transformed into the other buffer while this one is
-      // consumed; one barrier per chunk
-      if (ch + 1 < nchunks) transform((ch + 1) * NC, Ybuf + ((ch + 1) & 1) * NC * NC * 32);
       const float2 *Y = Ybuf + (ch & 1) * NC * NC * 32;
       const int b0 = ch * NC;
       const int kmax = min(NC, nci - b0);
@@ -191,6 +195,12 @@ __global__ void __launch_bounds__(32 << D) half_step_split_kernel(
         for (int k = 0; k < NC; ++k) consume(k);
       } else {
         for (int k = 0; k < kmax; ++k) consume(k);
+      }
+      // the next chunk (already loaded) goes into the other buffer and the
+      // loads of the one after are issued before the barrier
+      if (ch + 1 < nchunks) {
+        transform((ch + 1) * NC, Ybuf + ((ch + 1) & 1) * NC * NC * 32);
+        if (ch + 2 < nchunks) load((ch + 2) * NC);
       }
       __syncthreads();
     }
