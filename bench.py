@@ -332,15 +332,83 @@ def run_ours(args):
     return 0
 
 
+def batch_problems(seed=0, n=512, lam=0.9):
+    """Ragged 2-D workload: N uniform in {32,64,128,256} (square grids), m
+    uniform in {2..6}, boundary uniform in {periodic, Dirichlet, Neumann},
+    u0 = 1-4 Gaussian pulses (widths U[0.05,0.2], amplitudes N(0,1), centres
+    U[0,1)^2), v0 = 0, c dt/h = 0.9; numpy PCG64 with the given seed."""
+    from paper_1802_05246_b300 import inputs as I
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        Np = int(rng.choice([32, 64, 128, 256]))
+        m = int(rng.integers(2, 7))
+        bc = int(rng.integers(0, 3))
+        cen, wid, amp = I.random_pulses(rng, 2, 1, 4, 0.05, 0.2)
+        out.append((Np, m, bc, cen, wid, amp))
+    return out
+
+
+def run_batch(args):
+    """Ragged batch of 512 2-D problems, both variants, FP64 and split."""
+    import torch
+
+    import paper_1802_05246_b300 as hb
+    from paper_1802_05246_b300 import inputs as I
+
+    torch.cuda.set_device(0)
+    specs = batch_problems()
+    lam = 0.9
+    results = {}
+    for variant in (hb.DISSIPATIVE, hb.CONSERVATIVE):
+        probs = [(2, m, Np, 1.0, 1.0 / Np, lam / Np, variant, bc) for (Np, m, bc, _, _, _) in specs]
+        for prec in (hb.FP64, hb.SPLIT32):
+            b = hb.HermiteBatch(probs, precision=prec)
+            s = torch.cuda.Stream()
+            b.set_stream(s)
+            items, blocks, tune_ms = b.autotune()
+            for (Np, m, bc, cen, wid, amp), g in zip(specs, b.problems):
+                u0 = I.gaussian_data(2, m, Np, 1.0 / Np, bc, 0, cen, wid, amp)
+                g.set_state(u0, np.zeros((g.nodes(0), m * m)))
+            b.step(args.warmup)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(s)
+            b.step(args.steps)
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            results[(variant, prec)] = {"value": b.dof_per_step * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                                        "autotune": {"item_nodes": items, "blocks_per_sm": blocks, "ms": tune_ms}}
+            b.close()
+    line = {
+        "metric": METRIC, "value": results[(0, 1)]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": results[(0, 1)]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
+        "config": {"workload": "ragged batch of 512 2-D problems (N in {32,64,128,256}^2, m in 2..6, "
+                               "periodic/Dirichlet/Neumann, 1-4 Gaussian pulses, c*dt/h=0.9), one persistent "
+                               "launch per size group per half-step, graph-captured full steps",
+                   "step": "one full time step of all 512 problems"},
+        "by_variant_precision": {f"{'dissipative' if v == 0 else 'conservative'}_{'fp64' if p == 0 else 'split'}": r
+                                 for (v, p), r in results.items()},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grid3d", choices=["grid3d", "batch2d"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch2d":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -195,6 +195,57 @@ int hermite_operator(hermite_ctx *ctx, int which, double *out, int *rows, int *c
  * serialised by the caller.  The context's device must be current. */
 int hermite_energy_noalloc(hermite_ctx *ctx, int grid, const double *level, int64_t ld, double *out_dev);
 
+/* ------------------------------------------------------------------------
+ * Ragged batches.  Many independent problems -- differing N, m, boundary
+ * condition, variant and time step, one dimension d for the whole batch --
+ * advanced together: every half-step of the batch is one persistent launch
+ * per group of problems with similar output counts, whose blocks take
+ * (problem, node range) items from a work counter (longest items first), so
+ * small and large grids share the GPU in one launch.  A full step is
+ * captured once as a CUDA graph and replayed.  The method per problem is the
+ * same as for a single context (Sec. 3 / 4); no data moves between problems.
+ * ---------------------------------------------------------------------- */
+typedef struct hermite_batch hermite_batch;
+
+/* Create nprob problems; arrays of length nprob give each problem's
+ * hermite_create arguments.  precision: HERMITE_FP64 or HERMITE_SPLIT32 for
+ * all problems.  Batch problems carry no energy forms (hermite_energy on them
+ * returns HERMITE_ERR_STATE).  On error *out is NULL and
+ * hermite_batch_last_error(NULL) names the failing problem. */
+int hermite_batch_create(int nprob, const int *d, const int *m, const int64_t *N, const double *c,
+                         const double *h, const double *dt, const int *variant, const int *bc,
+                         int precision, hermite_batch **out);
+void hermite_batch_destroy(hermite_batch *b);
+
+/* Borrowed context of problem p (owned by the batch; do not destroy it) for
+ * hermite_set_state / set_state2 / get_state / get_grid.  NULL if p is out of
+ * range.  All problems must have taken the same number of half-steps when
+ * hermite_batch_step is called. */
+hermite_ctx *hermite_batch_problem(hermite_batch *b, int p);
+
+/* Stream for the batch and all its problems.  Graph capture needs a
+ * non-default stream; on the legacy default stream the batch launches its
+ * kernels directly. */
+int hermite_batch_set_stream(hermite_batch *b, void *stream);
+
+/* Advance every problem by nsteps full steps (device work only). */
+int hermite_batch_step(hermite_batch *b, int64_t nsteps);
+
+/* DOF-updates of one full step of the whole batch (both half-steps). */
+int64_t hermite_batch_dof_per_step(const hermite_batch *b);
+
+/* Time one full step for each candidate (item size in nodes x resident blocks
+ * per SM) and keep the fastest; returns the choice and its time.  Advances the
+ * loaded state by three full steps per candidate: call it before setting the
+ * initial data.  Needs a non-default stream. */
+int hermite_batch_autotune(hermite_batch *b, int *item_nodes, int *blocks_per_sm, double *ms_per_step);
+
+/* Set the item size (>= 32 nodes) and resident blocks per SM (1..32) directly. */
+int hermite_batch_config(hermite_batch *b, int item_nodes, int blocks_per_sm);
+
+/* Message of the last failed call on this batch (NULL: last failed create). */
+const char *hermite_batch_last_error(const hermite_batch *b);
+
 /* Message of the last failed call on this context ("" if none).  With a NULL
  * context: the message of the last failed hermite_create in this thread. */
 const char *hermite_last_error(const hermite_ctx *ctx);

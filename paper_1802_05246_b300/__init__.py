@@ -31,7 +31,9 @@ EXPORTS = [
     "hermite_set_state2", "hermite_step", "hermite_advance_half", "hermite_half_steps", "hermite_time",
     "hermite_get_state", "hermite_get_grid", "hermite_set_grid", "hermite_get_grid_device", "hermite_energy",
     "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error", "hermite_energy_noalloc",
-    "hermite_create_ex",
+    "hermite_create_ex", "hermite_batch_create", "hermite_batch_destroy", "hermite_batch_problem",
+    "hermite_batch_set_stream", "hermite_batch_step", "hermite_batch_dof_per_step", "hermite_batch_autotune",
+    "hermite_batch_config", "hermite_batch_last_error",
 ]
 
 
@@ -76,6 +78,15 @@ def lib():
         "hermite_last_error": (ctypes.c_char_p, [vp]),
         "hermite_energy_noalloc": (c_int, [vp, c_int, vp, i64, vp]),
         "hermite_create_ex": (c_int, [c_int, c_int, i64, c_dbl, c_dbl, c_dbl, c_int, c_int, c_int, ctypes.POINTER(vp)]),
+        "hermite_batch_create": (c_int, [c_int, vp, vp, vp, vp, vp, vp, vp, vp, c_int, ctypes.POINTER(vp)]),
+        "hermite_batch_destroy": (None, [vp]),
+        "hermite_batch_problem": (vp, [vp, c_int]),
+        "hermite_batch_set_stream": (c_int, [vp, vp]),
+        "hermite_batch_step": (c_int, [vp, i64]),
+        "hermite_batch_dof_per_step": (i64, [vp]),
+        "hermite_batch_autotune": (c_int, [vp, ip, ip, dp]),
+        "hermite_batch_config": (c_int, [vp, c_int, c_int]),
+        "hermite_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -122,7 +133,8 @@ class Hermite:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().hermite_destroy(self._h)
+            if getattr(self, "_owned", True):
+                lib().hermite_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -204,3 +216,77 @@ class Hermite:
         M = np.empty((r.value, c.value))
         self._check(lib().hermite_operator(self._h, which, _ptr(M), ctypes.byref(r), ctypes.byref(c)))
         return M
+
+
+def _borrow(handle, d, m, N, c, h, dt, variant, bc, precision):
+    """A non-owning Hermite view of a context that belongs to a batch."""
+    g = Hermite.__new__(Hermite)
+    g._h = ctypes.c_void_p(handle)
+    g._owned = False
+    g.d, g.m, g.N, g.c, g.h, g.dt = int(d), int(m), int(N), float(c), float(h), float(dt)
+    g.variant, g.bc, g.precision = int(variant), int(bc), int(precision)
+    nu, nv = ctypes.c_int(), ctypes.c_int()
+    lib().hermite_ncoef(g._h, ctypes.byref(nu), ctypes.byref(nv))
+    g.Nu, g.Nv = nu.value, nv.value
+    return g
+
+
+class HermiteBatch:
+    """Ragged batch of problems advanced together (see hermite_batch_create).
+
+    problems: sequence of (d, m, N, c, h, dt, variant, bc) tuples, one d for all."""
+
+    def __init__(self, problems, precision=FP64):
+        L = lib()
+        probs = [tuple(p) for p in problems]
+        n = len(probs)
+        cols = list(zip(*probs))
+        arr = lambda typ, xs: (typ * n)(*xs)
+        self._b = ctypes.c_void_p()
+        rc = L.hermite_batch_create(n, arr(ctypes.c_int, cols[0]), arr(ctypes.c_int, cols[1]),
+                                    arr(ctypes.c_int64, cols[2]), arr(ctypes.c_double, cols[3]),
+                                    arr(ctypes.c_double, cols[4]), arr(ctypes.c_double, cols[5]),
+                                    arr(ctypes.c_int, cols[6]), arr(ctypes.c_int, cols[7]), int(precision),
+                                    ctypes.byref(self._b))
+        if rc != 0:
+            raise HermiteError(rc, L.hermite_batch_last_error(None).decode())
+        self.precision = int(precision)
+        self.problems = [_borrow(L.hermite_batch_problem(self._b, i), *probs[i], precision) for i in range(n)]
+
+    def _check(self, rc):
+        if rc != 0:
+            raise HermiteError(rc, lib().hermite_batch_last_error(self._b).decode())
+
+    def problem(self, p):
+        return self.problems[p]
+
+    def set_stream(self, stream):
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(lib().hermite_batch_set_stream(self._b, raw))
+
+    def step(self, n=1):
+        self._check(lib().hermite_batch_step(self._b, int(n)))
+
+    @property
+    def dof_per_step(self):
+        return int(lib().hermite_batch_dof_per_step(self._b))
+
+    def autotune(self):
+        a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(lib().hermite_batch_autotune(self._b, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)))
+        return a.value, b.value, ms.value
+
+    def config(self, item_nodes, blocks_per_sm):
+        self._check(lib().hermite_batch_config(self._b, int(item_nodes), int(blocks_per_sm)))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().hermite_batch_destroy(self._b)
+            self._b = None
+            self.problems = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -194,6 +194,15 @@ int hermite_create(int d, int m, int64_t N, double c, double h, double dt, int v
 
 int hermite_create_ex(int d, int m, int64_t N, double c, double h, double dt, int variant, int bc,
                       int precision, hermite_ctx **out) {
+  return hermite::create_context(d, m, N, c, h, dt, variant, bc, precision, true, out);
+}
+
+}  // extern "C"
+
+namespace hermite {
+
+int create_context(int d, int m, int64_t N, double c, double h, double dt, int variant, int bc, int precision,
+                   bool with_energy, hermite_ctx **out) {
   if (precision != HERMITE_FP64 && precision != HERMITE_SPLIT32) {
     g_create_error = "unknown precision";
     if (out) *out = nullptr;
@@ -270,7 +279,8 @@ int hermite_create_ex(int d, int m, int64_t N, double c, double h, double dt, in
   if (rc == HERMITE_OK) rc = build_parity_tables(ctx);
   if (rc == HERMITE_OK) rc = build_operator(ctx, false, ctx->M, ctx->nco, ctx->nci);
   if (rc == HERMITE_OK && cons) rc = build_operator(ctx, true, ctx->Mstart, ctx->Nu, ctx->Nu + ctx->Nv);
-  if (rc == HERMITE_OK) rc = build_energy_forms(ctx);
+  ctx->has_energy = with_energy;
+  if (rc == HERMITE_OK && with_energy) rc = build_energy_forms(ctx);
   ctx->precision = precision;
   if (rc == HERMITE_OK && precision == HERMITE_SPLIT32) {
     for (int g = 0; g < 2; ++g) alloc((void **)&ctx->fgrid[g], sizeof(float2) * ctx->ncoef * ctx->ld[g], "split grid");
@@ -291,6 +301,10 @@ int hermite_create_ex(int d, int m, int64_t N, double c, double h, double dt, in
   *out = ctx;
   return HERMITE_OK;
 }
+
+}  // namespace hermite
+
+extern "C" {
 
 void hermite_destroy(hermite_ctx *ctx) {
   if (!ctx) return;
@@ -393,6 +407,7 @@ int hermite_set_grid(hermite_ctx *ctx, int grid, const double *u, const double *
 
 int hermite_energy(hermite_ctx *ctx, double out[3]) {
   if (!ctx || !out) return ctx ? fail(ctx, HERMITE_ERR_ARG, "out is NULL") : HERMITE_ERR_ARG;
+  if (!ctx->has_energy) return fail(ctx, HERMITE_ERR_STATE, "this context was created without energy forms");
   int rc = HERMITE_OK;
   double host[4] = {0, 0, 0, 0};
   if (is_split(ctx)) {

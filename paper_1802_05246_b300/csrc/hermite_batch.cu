@@ -1,0 +1,649 @@
+// Ragged batches: many problems (differing N, m, boundary condition and
+// variant, one dimension d per batch) advanced together.  Each half-step of
+// the whole batch is one persistent launch per output-size group: blocks take
+// (problem, node range) items from an atomic counter until the list is empty,
+// so large and small problems share the GPU without one launch per problem
+// and without any inter-block waiting.  Items are ordered longest first.  A
+// full step (two half-steps) is captured once as a CUDA graph and replayed.
+// A small autotuner times the item size and the number of resident blocks.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hermite_internal.h"
+
+namespace hermite {
+namespace {
+
+struct BatchItem {
+  int prob;
+  int64_t n0, n1;
+};
+
+struct BatchDesc {
+  Geometry g;
+  const void *src;
+  void *dst;
+  const double *M;
+  const float2 *Mc;
+  const int16_t *outrow;
+  const int8_t *npc;
+  const int8_t *par;
+  int nci, nco, sub;
+};
+
+template <int D>
+__device__ __forceinline__ void b_corners(const Geometry &g, int64_t t, int64_t *idx, int *gmask) {
+  int64_t ti[D];
+  int64_t r = t;
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i) {
+    ti[i] = r % g.n_dst;
+    r /= g.n_dst;
+  }
+  int64_t si[D][2];
+  int gh[D][2];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int64_t s = g.dst == 1 ? ti[i] + b : ti[i] - 1 + b;
+      int ghost = 0;
+      if (g.bc == HERMITE_PERIODIC) {
+        if (s < 0) s += g.n_src;
+        if (s >= g.n_src) s -= g.n_src;
+      } else if (s < 0) {
+        s = 0;
+        ghost = 1;
+      } else if (s >= g.n_src) {
+        s = g.n_src - 1;
+        ghost = 1;
+      }
+      si[i][b] = s;
+      gh[i][b] = ghost;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < (1 << D); ++s) {
+    int64_t id = 0;
+    int mask = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const int bit = (s >> (D - 1 - i)) & 1;
+      id = id * g.n_src + si[i][bit];
+      if (gh[i][bit]) mask |= 1 << (D - 1 - i);
+    }
+    idx[s] = id;
+    gmask[s] = mask;
+  }
+}
+
+__device__ __forceinline__ bool b_negates(int bc, int mask, int pb) {
+  int neg = __popc(mask & pb) & 1;
+  if (bc == HERMITE_DIRICHLET) neg ^= __popc(mask) & 1;
+  return neg != 0;
+}
+
+// ---------------------------------------------------------------- FP64
+constexpr int kBT = 128;
+
+template <int D, int CH>
+__global__ void __launch_bounds__(kBT) batch_f64_kernel(const BatchDesc *__restrict__ descs,
+                                                        const BatchItem *__restrict__ items, int nitems,
+                                                        unsigned *counter) {
+  constexpr int NC = 1 << D;
+  __shared__ double zb[NC * kBT];
+  __shared__ int item_s;
+  double *myz = zb + threadIdx.x;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = item_s;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem I = items[it];
+    const BatchDesc P = descs[I.prob];
+    const double *src = static_cast<const double *>(P.src);
+    double *dst = static_cast<double *>(P.dst);
+    for (int64_t t = I.n0 + threadIdx.x; t < I.n1; t += kBT) {
+      int64_t idx[NC];
+      int gm[NC];
+      b_corners<D>(P.g, t, idx, gm);
+      for (int c0 = 0; c0 < P.nco; c0 += CH) {
+        double acc[CH];
+        int po[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          acc[j] = 0.0;
+          po[j] = (c0 + j < P.nco) ? P.par[c0 + j] : 0;
+        }
+        for (int b = 0; b < P.nci; ++b) {
+          const double *plane = src + (size_t)b * P.g.ld_src;
+          const int pb = P.par[b];
+          double x[NC];
+#pragma unroll
+          for (int s = 0; s < NC; ++s) {
+            double v = __ldg(plane + idx[s]);
+            if (gm[s] && b_negates(P.g.bc, gm[s], pb)) v = -v;
+            x[s] = v;
+          }
+#pragma unroll
+          for (int bm = 1; bm < NC; bm <<= 1)
+#pragma unroll
+            for (int i = 0; i < NC; ++i)
+              if (!(i & bm)) {
+                const double a = x[i], c = x[i | bm];
+                x[i] = a + c;
+                x[i | bm] = a - c;
+              }
+#pragma unroll
+          for (int s = 0; s < NC; ++s) myz[s * kBT] = x[s];
+#pragma unroll
+          for (int j = 0; j < CH; ++j)
+            if (c0 + j < P.nco)
+              acc[j] = fma(__ldg(P.M + (size_t)(c0 + j) * P.nci + b), myz[(po[j] ^ pb) * kBT], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          if (c0 + j < P.nco) {
+            double *o = dst + (size_t)(c0 + j) * P.g.ld_dst + t;
+            *o = P.sub ? acc[j] - *o : acc[j];
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- split
+__device__ __forceinline__ float2 b_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 b_df_add(float2 a, float2 b) {
+  float2 t = b_two_sum(a.x, b.x);
+  t.y = __fadd_rn(t.y, __fadd_rn(a.y, b.y));
+  return t;
+}
+__device__ __forceinline__ float2 b_df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 b_df_norm(float2 a) {
+  const float s = __fadd_rn(a.x, a.y);
+  return make_float2(s, __fsub_rn(a.y, __fsub_rn(s, a.x)));
+}
+__device__ __forceinline__ void b_df_fma(float2 &acc, const float2 m, const float2 y) {
+  const float p = __fmul_rn(m.x, y.x);
+  const float e = __fmaf_rn(m.x, y.x, -p);
+  const float2 s = b_two_sum(acc.x, p);
+  float c = __fadd_rn(acc.y, __fadd_rn(s.y, e));
+  c = __fmaf_rn(m.x, y.y, c);
+  c = __fmaf_rn(m.y, y.x, c);
+  acc = make_float2(s.x, c);
+}
+
+// one item = a range of target nodes processed 32 at a time by 2^d class warps
+template <int D, int NOMAX>
+__global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *__restrict__ descs,
+                                                              const BatchItem *__restrict__ items, int nitems,
+                                                              unsigned *counter) {
+  constexpr int NC = 1 << D;
+  __shared__ float2 Y[NC * NC * 32];
+  __shared__ int item_s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = item_s;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem I = items[it];
+    const BatchDesc P = descs[I.prob];
+    const float2 *src = static_cast<const float2 *>(P.src);
+    float2 *dst = static_cast<float2 *>(P.dst);
+    const int np = P.npc[w];
+    for (int64_t base = I.n0; base < I.n1; base += 32) {
+      const int64_t t = base + lane;
+      const bool valid = t < I.n1;
+      int64_t idx[NC];
+      int gm[NC];
+      if (valid) {
+        b_corners<D>(P.g, t, idx, gm);
+      } else {
+#pragma unroll
+        for (int s = 0; s < NC; ++s) {
+          idx[s] = 0;
+          gm[s] = 0;
+        }
+      }
+      float2 acc[NOMAX];
+#pragma unroll
+      for (int j = 0; j < NOMAX; ++j) acc[j] = make_float2(0.f, 0.f);
+      for (int b0 = 0; b0 < P.nci; b0 += NC) {
+        const int b = b0 + w;
+        if (b < P.nci) {
+          const float2 *plane = src + (size_t)b * P.g.ld_src;
+          const int pb = P.par[b];
+          float2 x[NC];
+#pragma unroll
+          for (int s = 0; s < NC; ++s) {
+            float2 v = plane[idx[s]];
+            if (gm[s] && b_negates(P.g.bc, gm[s], pb)) v = b_df_neg(v);
+            x[s] = v;
+          }
+#pragma unroll
+          for (int bm = 1; bm < NC; bm <<= 1)
+#pragma unroll
+            for (int i = 0; i < NC; ++i)
+              if (!(i & bm)) {
+                const float2 a = x[i], c = x[i | bm];
+                x[i] = b_df_add(a, c);
+                x[i | bm] = b_df_add(a, b_df_neg(c));
+              }
+#pragma unroll
+          for (int q = 0; q < NC; ++q) Y[(w * NC + q) * 32 + lane] = x[q];
+        }
+        __syncthreads();
+        const int kmax = min(NC, P.nci - b0);
+        for (int k = 0; k < kmax; ++k) {
+          const int bb = b0 + k;
+          const float2 y = Y[(k * NC + (w ^ P.par[bb])) * 32 + lane];
+          const float4 *mrow = reinterpret_cast<const float4 *>(P.Mc + ((size_t)w * P.nci + bb) * NOMAX);
+#pragma unroll
+          for (int j = 0; j < NOMAX / 2; ++j) {
+            const float4 mm = __ldg(mrow + j);
+            b_df_fma(acc[2 * j], make_float2(mm.x, mm.y), y);
+            b_df_fma(acc[2 * j + 1], make_float2(mm.z, mm.w), y);
+          }
+        }
+        __syncthreads();
+      }
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < NOMAX; ++j) {
+          if (j < np) {
+            const int row = P.outrow[w * NOMAX + j];
+            float2 *o = dst + (size_t)row * P.g.ld_dst + t;
+            float2 r = b_df_norm(acc[j]);
+            if (P.sub) r = b_df_norm(b_df_add(r, b_df_neg(*o)));
+            *o = r;
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+}  // namespace hermite
+
+struct hermite_batch {
+  int d = 0, precision = 0, nprob = 0;
+  std::vector<hermite_ctx *> probs;
+  cudaStream_t stream = nullptr;
+  hermite::BatchDesc *d_desc[2] = {nullptr, nullptr};
+  struct Group {
+    int tmpl;  // CH (FP64) or NOMAX (split)
+    hermite::BatchItem *d_items;
+    int nitems;
+  };
+  std::vector<Group> groups[2];
+  unsigned *d_counters = nullptr;
+  int ncounters = 0;
+  int item_nodes = 1024, blocks_per_sm = 2, nsm = 148;
+  cudaGraphExec_t graph = nullptr;
+  int64_t half = 0;
+  std::string err;
+};
+
+namespace hermite {
+namespace {
+
+thread_local std::string g_batch_error;
+
+bool bok(hermite_batch *b, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return true;
+  b->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+int half_dst(const hermite_ctx *ctx, int64_t half) {
+  if (ctx->variant == HERMITE_CONSERVATIVE) return (half % 2 == 0) ? HERMITE_PRIMAL : HERMITE_DUAL;
+  return (half % 2 == 0) ? HERMITE_DUAL : HERMITE_PRIMAL;
+}
+
+void free_items(hermite_batch *b) {
+  for (int k = 0; k < 2; ++k) {
+    for (auto &gr : b->groups[k]) cudaFree(gr.d_items);
+    b->groups[k].clear();
+  }
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+int group_key(const hermite_batch *b, const hermite_ctx *ctx) {
+  if (b->precision == HERMITE_SPLIT32) return ctx->nomax;
+  return ctx->nco <= 16 ? 16 : (ctx->nco <= 32 ? 32 : 48);
+}
+
+int build_items(hermite_batch *b) {
+  free_items(b);
+  for (int k = 0; k < 2; ++k) {
+    std::vector<int> keys;
+    for (auto *c : b->probs) {
+      const int key = group_key(b, c);
+      if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+    }
+    for (int key : keys) {
+      struct HostItem {
+        BatchItem it;
+        double cost;
+      };
+      std::vector<HostItem> h;
+      for (int p = 0; p < b->nprob; ++p) {
+        const hermite_ctx *c = b->probs[p];
+        if (group_key(b, c) != key) continue;
+        const int dst = half_dst(c, k);
+        const int64_t n = c->nodes[dst];
+        for (int64_t n0 = 0; n0 < n; n0 += b->item_nodes) {
+          HostItem hi;
+          hi.it.prob = p;
+          hi.it.n0 = n0;
+          hi.it.n1 = std::min<int64_t>(n, n0 + b->item_nodes);
+          hi.cost = (double)(hi.it.n1 - hi.it.n0) * c->nci * c->nco;
+          h.push_back(hi);
+        }
+      }
+      std::stable_sort(h.begin(), h.end(), [](const HostItem &a, const HostItem &c) { return a.cost > c.cost; });
+      std::vector<BatchItem> items(h.size());
+      for (size_t i = 0; i < h.size(); ++i) items[i] = h[i].it;
+      hermite_batch::Group gr{key, nullptr, (int)items.size()};
+      if (!bok(b, cudaMalloc(&gr.d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)), "cudaMalloc items") ||
+          !bok(b, cudaMemcpy(gr.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice),
+               "items copy"))
+        return HERMITE_ERR_CUDA;
+      b->groups[k].push_back(gr);
+    }
+  }
+  const int need = (int)(b->groups[0].size() + b->groups[1].size());
+  if (need > b->ncounters) {
+    cudaFree(b->d_counters);
+    b->d_counters = nullptr;
+    if (!bok(b, cudaMalloc(&b->d_counters, sizeof(unsigned) * need), "cudaMalloc counters")) return HERMITE_ERR_ALLOC;
+    b->ncounters = need;
+  }
+  return HERMITE_OK;
+}
+
+int build_descs(hermite_batch *b) {
+  for (int k = 0; k < 2; ++k) {
+    std::vector<BatchDesc> h(b->nprob);
+    for (int p = 0; p < b->nprob; ++p) {
+      const hermite_ctx *c = b->probs[p];
+      const int dst = half_dst(c, k);
+      BatchDesc &ds = h[p];
+      ds.g = make_geometry(c, dst);
+      if (b->precision == HERMITE_SPLIT32) {
+        ds.src = c->fgrid[1 - dst];
+        ds.dst = c->fgrid[dst];
+      } else {
+        ds.src = c->grid[1 - dst];
+        ds.dst = c->grid[dst];
+      }
+      ds.M = c->M;
+      ds.Mc = c->Mc;
+      ds.outrow = c->outrow;
+      ds.npc = c->npc;
+      ds.par = c->par_in;
+      ds.nci = c->nci;
+      ds.nco = c->nco;
+      ds.sub = c->variant == HERMITE_CONSERVATIVE ? 1 : 0;
+    }
+    if (!bok(b, cudaMalloc(&b->d_desc[k], sizeof(BatchDesc) * b->nprob), "cudaMalloc descs") ||
+        !bok(b, cudaMemcpy(b->d_desc[k], h.data(), sizeof(BatchDesc) * b->nprob, cudaMemcpyHostToDevice),
+             "descs copy"))
+      return HERMITE_ERR_CUDA;
+  }
+  return HERMITE_OK;
+}
+
+template <int D>
+int launch_group(hermite_batch *b, int k, const hermite_batch::Group &gr, unsigned *counter) {
+  const unsigned blocks = (unsigned)(b->nsm * b->blocks_per_sm);
+  if (b->precision == HERMITE_SPLIT32) {
+    switch (gr.tmpl) {
+      case 8: batch_split_kernel<D, 8><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 16: batch_split_kernel<D, 16><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      default: batch_split_kernel<D, 32><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+    }
+  } else {
+    switch (gr.tmpl) {
+      case 16: batch_f64_kernel<D, 16><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 32: batch_f64_kernel<D, 32><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      default: batch_f64_kernel<D, 48><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+    }
+  }
+  return bok(b, cudaGetLastError(), "batch kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+// enqueue one half-step of every problem (parity k): per group, reset its
+// work counter and launch the persistent kernel
+int enqueue_half(hermite_batch *b, int k) {
+  int ci = (k == 0) ? 0 : (int)b->groups[0].size();
+  for (const auto &gr : b->groups[k]) {
+    unsigned *counter = b->d_counters + ci++;
+    if (!bok(b, cudaMemsetAsync(counter, 0, sizeof(unsigned), b->stream), "counter reset")) return HERMITE_ERR_CUDA;
+    int rc;
+    switch (b->d) {
+      case 1: rc = launch_group<1>(b, k, gr, counter); break;
+      case 2: rc = launch_group<2>(b, k, gr, counter); break;
+      default: rc = launch_group<3>(b, k, gr, counter); break;
+    }
+    if (rc) return rc;
+  }
+  return HERMITE_OK;
+}
+
+int sync_half(hermite_batch *b) {
+  const int64_t h0 = b->probs[0]->half;
+  for (auto *c : b->probs)
+    if (c->half != h0) {
+      b->err = "problems of a batch must have taken the same number of half-steps";
+      return HERMITE_ERR_STATE;
+    }
+  b->half = h0;
+  return HERMITE_OK;
+}
+
+void set_half(hermite_batch *b) {
+  for (auto *c : b->probs) c->half = b->half;
+}
+
+}  // namespace
+}  // namespace hermite
+
+using namespace hermite;
+
+extern "C" {
+
+int hermite_batch_create(int nprob, const int *d, const int *m, const int64_t *N, const double *c, const double *h,
+                         const double *dt, const int *variant, const int *bc, int precision, hermite_batch **out) {
+  if (!out || nprob < 1 || !d || !m || !N || !c || !h || !dt || !variant || !bc) {
+    g_batch_error = "invalid argument to hermite_batch_create";
+    return HERMITE_ERR_ARG;
+  }
+  *out = nullptr;
+  for (int p = 1; p < nprob; ++p)
+    if (d[p] != d[0]) {
+      g_batch_error = "all problems of a batch must have the same dimension";
+      return HERMITE_ERR_ARG;
+    }
+  hermite_batch *b = new hermite_batch;
+  b->d = d[0];
+  b->precision = precision;
+  b->nprob = nprob;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  int rc = HERMITE_OK;
+  for (int p = 0; p < nprob && rc == HERMITE_OK; ++p) {
+    hermite_ctx *ctx = nullptr;
+    rc = create_context(d[p], m[p], N[p], c[p], h[p], dt[p], variant[p], bc[p], precision, false, &ctx);
+    if (rc) {
+      g_batch_error = "problem " + std::to_string(p) + ": " + hermite_last_error(nullptr);
+      break;
+    }
+    b->probs.push_back(ctx);
+  }
+  if (rc == HERMITE_OK) rc = build_descs(b);
+  if (rc == HERMITE_OK) rc = build_items(b);
+  if (rc != HERMITE_OK) {
+    if (g_batch_error.empty()) g_batch_error = b->err;
+    hermite_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return HERMITE_OK;
+}
+
+void hermite_batch_destroy(hermite_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  free_items(b);
+  for (int k = 0; k < 2; ++k) cudaFree(b->d_desc[k]);
+  cudaFree(b->d_counters);
+  for (auto *c : b->probs) hermite_destroy(c);
+  delete b;
+}
+
+hermite_ctx *hermite_batch_problem(hermite_batch *b, int p) {
+  if (!b || p < 0 || p >= b->nprob) return nullptr;
+  return b->probs[p];
+}
+
+int hermite_batch_set_stream(hermite_batch *b, void *stream) {
+  if (!b) return HERMITE_ERR_ARG;
+  b->stream = (cudaStream_t)stream;
+  for (auto *c : b->probs) c->stream = b->stream;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return HERMITE_OK;
+}
+
+int hermite_batch_step(hermite_batch *b, int64_t nsteps) {
+  if (!b) return HERMITE_ERR_ARG;
+  if (nsteps < 0) {
+    b->err = "nsteps < 0";
+    return HERMITE_ERR_ARG;
+  }
+  int rc = sync_half(b);
+  if (rc) return rc;
+  if (b->half % 2 != 0 || b->stream == nullptr) {
+    // direct launches (odd start, or the legacy stream, which cannot be captured)
+    for (int64_t i = 0; i < 2 * nsteps; ++i) {
+      rc = enqueue_half(b, (int)(b->half % 2));
+      if (rc) return rc;
+      b->half += 1;
+    }
+    set_half(b);
+    return HERMITE_OK;
+  }
+  if (!b->graph && nsteps > 0) {
+    cudaGraph_t g = nullptr;
+    if (!bok(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture"))
+      return HERMITE_ERR_CUDA;
+    int rc1 = enqueue_half(b, 0);
+    int rc2 = rc1 ? rc1 : enqueue_half(b, 1);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc2) {
+      if (g) cudaGraphDestroy(g);
+      return rc2;
+    }
+    if (!bok(b, e, "end capture")) return HERMITE_ERR_CUDA;
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (!bok(b, e, "graph instantiate")) return HERMITE_ERR_CUDA;
+  }
+  for (int64_t i = 0; i < nsteps; ++i)
+    if (!bok(b, cudaGraphLaunch(b->graph, b->stream), "graph launch")) return HERMITE_ERR_CUDA;
+  b->half += 2 * nsteps;
+  set_half(b);
+  return HERMITE_OK;
+}
+
+int64_t hermite_batch_dof_per_step(const hermite_batch *b) {
+  if (!b) return -1;
+  int64_t s = 0;
+  for (auto *c : b->probs) s += (c->nodes[0] + c->nodes[1]) * (int64_t)c->nco;
+  return s;
+}
+
+int hermite_batch_autotune(hermite_batch *b, int *item_nodes, int *blocks_per_sm, double *ms_per_step) {
+  if (!b) return HERMITE_ERR_ARG;
+  if (!b->stream) {
+    b->err = "set a non-default stream before autotuning";
+    return HERMITE_ERR_STATE;
+  }
+  const int cand_items[] = {256, 1024, 4096};
+  const int cand_blocks[] = {1, 2, 4, 8};
+  double best = 1e30;
+  int bi = b->item_nodes, bb = b->blocks_per_sm;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = HERMITE_OK;
+  for (int in : cand_items) {
+    for (int bp : cand_blocks) {
+      b->item_nodes = in;
+      b->blocks_per_sm = bp;
+      rc = build_items(b);
+      if (rc) break;
+      rc = hermite_batch_step(b, 1);  // warm-up, builds the graph
+      if (rc) break;
+      cudaEventRecord(e0, b->stream);
+      rc = hermite_batch_step(b, 2);
+      if (rc) break;
+      cudaEventRecord(e1, b->stream);
+      if (!bok(b, cudaEventSynchronize(e1), "autotune sync")) {
+        rc = HERMITE_ERR_CUDA;
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 2 < best) {
+        best = ms / 2;
+        bi = in;
+        bb = bp;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  b->item_nodes = bi;
+  b->blocks_per_sm = bb;
+  rc = build_items(b);
+  if (item_nodes) *item_nodes = bi;
+  if (blocks_per_sm) *blocks_per_sm = bb;
+  if (ms_per_step) *ms_per_step = best;
+  return rc;
+}
+
+int hermite_batch_config(hermite_batch *b, int item_nodes, int blocks_per_sm) {
+  if (!b || item_nodes < 32 || blocks_per_sm < 1 || blocks_per_sm > 32) return HERMITE_ERR_ARG;
+  b->item_nodes = item_nodes;
+  b->blocks_per_sm = blocks_per_sm;
+  return build_items(b);
+}
+
+const char *hermite_batch_last_error(const hermite_batch *b) {
+  if (!b) return g_batch_error.c_str();
+  return b->err.c_str();
+}
+
+}  // extern "C"

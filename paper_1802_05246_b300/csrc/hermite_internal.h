@@ -65,6 +65,7 @@ struct hermite_ctx {
   // split precision (HERMITE_SPLIT32): state as FP32 hi + lo pairs; the FP64
   // grids above then serve as the staging copies for I/O and energies
   int precision = 0;
+  bool has_energy = true;      // energy forms built (batch problems skip them)
   float2 *fgrid[2] = {nullptr, nullptr};  // SoA [ncoef][ld] of (hi, lo)
   float2 *Mc = nullptr;        // operator rows grouped by output parity class
   float2 *Lf[hermite::kNumForms] = {nullptr, nullptr};  // energy factors split hi + lo
@@ -106,6 +107,8 @@ int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const
                        double *result_slot);
 
 Geometry make_geometry(const hermite_ctx *ctx, int dst);
+int create_context(int d, int m, int64_t N, double c, double h, double dt, int variant, int bc, int precision,
+                   bool with_energy, hermite_ctx **out);
 bool cuda_ok(hermite_ctx *ctx, cudaError_t e, const char *what);
 
 }  // namespace hermite
