@@ -34,6 +34,9 @@ EXPORTS = [
     "hermite_create_ex", "hermite_batch_create", "hermite_batch_destroy", "hermite_batch_problem",
     "hermite_batch_set_stream", "hermite_batch_step", "hermite_batch_dof_per_step", "hermite_batch_autotune",
     "hermite_batch_config", "hermite_batch_last_error",
+    # include/hermite_nn.h
+    "hnn_conv3x3_fwd", "hnn_flip_weights", "hnn_conv3x3_wgrad", "hnn_bias_grad", "hnn_mse", "hnn_adam",
+    "hnn_state_to_f32", "hnn_pack_state", "hnn_unpack_state", "hnn_make_pairs", "hnn_moments", "hnn_sqdiff",
 ]
 
 
@@ -87,6 +90,19 @@ def lib():
         "hermite_batch_autotune": (c_int, [vp, ip, ip, dp]),
         "hermite_batch_config": (c_int, [vp, c_int, c_int]),
         "hermite_batch_last_error": (ctypes.c_char_p, [vp]),
+        "hnn_conv3x3_fwd": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, c_int, c_int, c_int, c_int, vp, vp, vp]),
+        "hnn_flip_weights": (c_int, [vp, c_int, c_int, vp, vp]),
+        "hnn_conv3x3_wgrad": (c_int, [vp, vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, vp]),
+        "hnn_bias_grad": (c_int, [vp, i64, c_int, vp, vp]),
+        "hnn_mse": (c_int, [vp, vp, vp, i64, c_int, ctypes.c_float, vp, vp, vp]),
+        "hnn_adam": (c_int, [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             c_int, vp, vp]),
+        "hnn_state_to_f32": (c_int, [vp, vp, i64, c_int, c_int, c_dbl, vp, c_int, vp]),
+        "hnn_pack_state": (c_int, [vp, vp, i64, c_int, c_int, c_dbl, vp, vp, c_int, vp, vp]),
+        "hnn_unpack_state": (c_int, [vp, vp, vp, i64, c_int, c_int, c_dbl, vp, c_int, vp, vp, vp]),
+        "hnn_make_pairs": (c_int, [vp, vp, vp, c_int, i64, c_int, vp, vp, vp, c_int, vp, vp, vp]),
+        "hnn_moments": (c_int, [vp, vp, i64, c_int, vp, vp]),
+        "hnn_sqdiff": (c_int, [vp, vp, vp, vp, i64, c_int, c_int, c_dbl, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

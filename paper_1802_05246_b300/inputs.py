@@ -136,3 +136,26 @@ def random_pulses(rng: np.random.Generator, d: int, nmin: int, nmax: int, wmin: 
     widths = rng.uniform(wmin, wmax, size=n)
     amps = rng.normal(0.0, 1.0, size=n)
     return centres, widths, amps
+
+
+def gaussian_data_2d(q, N, h, bc, grid, centres, widths, amps):
+    """Same values as ``gaussian_data`` for d = 2, with the sum over pulses
+    taken as one matrix product (fast enough to generate thousands of
+    initial conditions)."""
+    centres = np.asarray(centres, dtype=np.float64).reshape(-1, 2)
+    ax = axis_coords(N, h, bc, grid)
+    L = N * h
+    n = ax.size
+    P = centres.shape[0]
+    gx = np.stack([float(amps[p]) * gaussian_1d(ax, q, h, centres[p, 0], float(widths[p]), L, bc) for p in range(P)])
+    gy = np.stack([gaussian_1d(ax, q, h, centres[p, 1], float(widths[p]), L, bc) for p in range(P)])
+    k = q + 1
+    U = gx.reshape(P, n * k).T @ gy.reshape(P, n * k)  # [(i, a), (j, b)]
+    return np.ascontiguousarray(U.reshape(n, k, n, k).transpose(0, 2, 1, 3)).reshape(n * n, k * k)
+
+
+def superstep_pulses(traj: int):
+    """Initial pulses of learned-stepper trajectory number traj: 1-6 pulses,
+    centres U[0,1)^2, widths U[0.05,0.15], amplitudes N(0,1), drawn from
+    numpy's PCG64 seeded with traj."""
+    return random_pulses(np.random.default_rng(traj), 2, 1, 6, 0.05, 0.15)

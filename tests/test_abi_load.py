@@ -1,5 +1,5 @@
 """The C-ABI library builds, loads without a GPU, and exports every symbol
-declared in include/hermite.h (no compute calls here)."""
+declared in include/*.h (no compute calls here)."""
 import ctypes
 import os
 import re
@@ -16,7 +16,7 @@ def declared_symbols():
     for h in HEADERS:
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names |= set(re.findall(r"\b(hermite_[a-z0-9_]+)\s*\(", text))
+        names |= set(re.findall(r"\b((?:hermite|hnn)_[a-z0-9_]+)\s*\(", text))
     return names
 
 
@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol(libpath):
     for s in sorted(syms):
         assert hasattr(L, s), s
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\b(hermite_[a-z0-9_]+)\b", out))
+    exported = set(re.findall(r"\b((?:hermite|hnn)_[a-z0-9_]+)\b", out))
     assert syms <= exported
 
 

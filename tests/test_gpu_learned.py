@@ -1,0 +1,115 @@
+"""Learned super-stepper pipeline on small batches: the solver-generated
+training levels, a short training run, and the residual check with its
+fallback to plain Hermite steps."""
+import numpy as np
+import pytest
+
+from tests.gpu_util import lib_built, need_gpu, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def st():
+    need_gpu()
+    lib_built()
+    from paper_1802_05246_b300.learned import SuperStepper
+
+    return SuperStepper(K=4)
+
+
+@pytest.fixture(scope="module")
+def levels(st):
+    return st.generate(range(6), nlev=3, chunk=4)
+
+
+def test_generated_levels_match_single_solver_runs(st, levels):
+    import paper_1802_05246_b300 as hb
+
+    lev = levels.cpu().numpy()
+    for t in (0, 5):  # first and second chunk (chunk 4: slots 2, 3 of chunk 2 unused)
+        u0 = st.initial_u(t)
+        g = hb.Hermite(*st.problem)
+        g.set_state(u0, np.zeros((st.n, st.Nv)))
+        for k in range(3):
+            if k:
+                g.step(st.K)
+            u, v = g.get_state()
+            s = np.concatenate([u, st.vscale * v], 1).astype(np.float32)
+            # the batch kernels may round differently from a single context (1e-13)
+            assert rel_l2(lev[t, k].astype(np.float64), s.astype(np.float64)) <= 1e-7, (t, k)
+        g.close()
+
+
+def test_short_training_reduces_the_loss(st, levels):
+    st.fit_stats(levels)
+    hist = st.train(levels, 60, batch=4, lr=2e-3, log_every=10)
+    first, last = hist[0][1], hist[-1][1]
+    assert np.isfinite(last) and last < 0.8 * first, hist
+
+
+def _batch(st, trajs):
+    import torch
+
+    import paper_1802_05246_b300 as hb
+
+    b = hb.HermiteBatch([st.problem] * len(trajs))
+    b.set_stream(torch.cuda.current_stream())
+    for p, t in enumerate(trajs):
+        b.problem(p).set_state(st.initial_u(t), np.zeros((st.n, st.Nv)))
+    return b
+
+
+def _states(st, b):
+    return [b.problem(p).get_state() for p in range(len(b.problems))]
+
+
+def test_fallback_reproduces_plain_hermite_steps(st):
+    trajs = [100, 101, 102]
+    e, r = st.calibrate(trajs)
+    assert np.all(e > 0) and np.all(r > 0) and st.kappa > 0
+    ref = _batch(st, trajs)
+    ref.step(st.K)
+    want = _states(st, ref)
+    b = _batch(st, trajs)
+    acc, est = st.advance(b, bar=1e-12)  # nothing passes this bar
+    assert not acc.any()
+    for (u, v), (wu, wv) in zip(_states(st, b), want):
+        assert rel_l2(np.concatenate([u, v], 1), np.concatenate([wu, wv], 1)) <= 1e-14
+
+
+def test_accepted_predictions_are_the_network_output(st):
+    import torch
+
+    trajs = [200, 201]
+    b = _batch(st, trajs)
+    X = st._alloc_states(2)
+    A = st._alloc_states(2)
+    st.gather(b, *X)
+    st.predict(X[0], X[1], A[0], A[1])
+    torch.cuda.synchronize()
+    pred = [(A[0][p].cpu().numpy(), A[1][p].cpu().numpy()) for p in range(2)]
+    kappa = st.kappa
+    st.kappa = 0.0  # every estimate is 0: all accepted
+    try:
+        acc, _ = st.advance(b, bar=1e-3)
+    finally:
+        st.kappa = kappa
+    assert acc.all()
+    for (u, v), (pu, pv) in zip(_states(st, b), pred):
+        assert np.array_equal(u, pu) and np.array_equal(v, pv)
+    b2 = _batch(st, trajs)
+    acc, _ = st.advance(b2, check=False)
+    for (u, v), (pu, pv) in zip(_states(st, b2), pred):
+        assert np.array_equal(u, pu) and np.array_equal(v, pv)
+
+
+def test_save_and_load_round_trip(st, tmp_path):
+    from paper_1802_05246_b300.learned import SuperStepper
+
+    path = str(tmp_path / "w.npz")
+    st.save(path)
+    st2 = SuperStepper.load(path)
+    assert np.array_equal(st2.net.get_params(), st.net.get_params())
+    assert st2.K == st.K and st2.kappa == st.kappa
+    assert np.array_equal(st2.dscale.cpu().numpy(), st.dscale.cpu().numpy())
