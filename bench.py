@@ -397,18 +397,126 @@ def run_batch(args):
     return 0
 
 
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1802_05246_b300", "weights", "superstepper_k16.npz")
+
+
+def run_learned(args):
+    """Learned super-stepper against plain Hermite steps on 256 fresh 2-D
+    problems (m = 3, 128^2 periodic, 1-6 Gaussian pulses, widths U[0.05,0.15]):
+    one benchmark step advances every problem by K = 16 full steps."""
+    import torch
+
+    import paper_1802_05246_b300 as hb
+    from paper_1802_05246_b300.learned import SuperStepper
+
+    torch.cuda.set_device(0)
+    st = SuperStepper.load(args.weights)
+    B, bar = 256, args.bar
+    trajs = list(range(3_000_000, 3_000_000 + B))
+    stream = torch.cuda.current_stream()
+    zero_v = np.zeros((st.n, st.Nv))
+    work = B * st.K * 2 * st.n * st.C0  # DOF-updates of K full steps of all problems
+
+    def fresh(prec):
+        b = hb.HermiteBatch([st.problem] * B, precision=prec)
+        b.set_stream(stream)
+        for p, t in enumerate(trajs):
+            b.problem(p).set_state(st.initial_u(t), zero_v)
+        return b
+
+    def timed(fn, before=None):
+        for _ in range(args.warmup):
+            if before:
+                before()
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            if before:
+                before()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    e_true, resid = st.evaluate(trajs)  # untimed: the true K-step error of every prediction
+    res = {}
+    for prec, name in ((hb.FP64, "fp64"), (hb.SPLIT32, "split")):
+        b = fresh(prec)
+        res[f"hermite_{name}_ms"] = timed(lambda: b.step(st.K))
+        b.close()
+        b = fresh(prec)
+        X = st._alloc_states(B)
+        st.gather(b, *X)
+        out = {}
+
+        def run():
+            out["acc"], out["est"] = st.advance(b, bar=bar)
+
+        res[f"learned_{name}_ms"] = timed(run, before=lambda: st.scatter(b, *X))
+        res[f"accepted_{name}"] = float(np.mean(out["acc"]))
+        res[f"false_accepts_{name}"] = int(np.sum(out["acc"] & (e_true > bar)))
+        A = st._alloc_states(B)
+        res[f"network_only_ms"] = timed(lambda: st.predict(X[0], X[1], A[0], A[1]))
+        b.close()
+    # the dominant kernel: the 64 -> 64 forward convolution at the inference batch
+    x = torch.zeros((B, 128, 128, 64), dtype=torch.bfloat16, device="cuda")
+    y = torch.empty_like(x)
+    w = torch.zeros((64, 9, 64), dtype=torch.bfloat16, device="cuda")
+    L = hb.lib()
+    conv_ms = timed(lambda: L.hnn_conv3x3_fwd(x.data_ptr(), w.data_ptr(), None, None, B, 128, 128, 64, 64, 8, 1,
+                                              y.data_ptr(), None, stream.cuda_stream))
+    conv_tflops = 2 * B * st.n * 9 * 64 * 64 / (conv_ms / 1e3) / 1e12
+    peak = peaks().get("bf16_tflops", 1800.0)
+    quant = lambda q: float(np.quantile(e_true, q))
+    sweep = {f"{b_:.0e}": {"accepted_by_estimate": float(np.mean(st.kappa * resid <= b_)),
+                           "true_error_within": float(np.mean(e_true <= b_))}
+             for b_ in (1e-3, 3e-3, 1e-2, 3e-2, 1e-1)}
+    line = {
+        "metric": "effective Hermite DOF-updates/s of K=16-step advances at rel. L2 <= bar (learned + fallback)",
+        "value": work / (res["learned_fp64_ms"] / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["learned_fp64_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (network) / f64 (check, fallback)", "data": "synthetic",
+        "config": {"workload": "256 2-D periodic problems, m=3, N=128^2, c*dt/h=0.9, 1-6 Gaussian pulses "
+                               "(widths U[0.05,0.15]), K=16 full steps per advance",
+                   "bar": bar, "kappa": st.kappa, "weights": os.path.relpath(args.weights, ROOT)},
+        "plain_hermite_fp64": {"value": work / (res["hermite_fp64_ms"] / 1e3), "ms_per_step": res["hermite_fp64_ms"]},
+        "plain_hermite_split": {"value": work / (res["hermite_split_ms"] / 1e3),
+                                "ms_per_step": res["hermite_split_ms"]},
+        "learned_split": {"value": work / (res["learned_split_ms"] / 1e3), "ms_per_step": res["learned_split_ms"],
+                          "accepted": res["accepted_split"], "false_accepts": res["false_accepts_split"]},
+        "accepted": res["accepted_fp64"], "false_accepts": res["false_accepts_fp64"],
+        "gain_vs_fp64": res["hermite_fp64_ms"] / res["learned_fp64_ms"],
+        "gain_vs_split": res["hermite_split_ms"] / res["learned_split_ms"],
+        "network_only_ms": res["network_only_ms"],
+        "true_error_quantiles": {"10%": quant(0.1), "50%": quant(0.5), "90%": quant(0.9), "max": quant(1.0)},
+        "bar_sweep": sweep,
+        "roofline": {"bound": "tensor", "kernel": "conv_fwd_kernel<64,64>", "achieved": conv_tflops, "peak": peak,
+                     "unit": "TFLOP/s", "frac": conv_tflops / peak, "traffic": None},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid3d", choices=["grid3d", "batch2d"])
+    ap.add_argument("--workload", default="grid3d", choices=["grid3d", "batch2d", "learned2d"])
+    ap.add_argument("--weights", default=LEARNED_WEIGHTS, help="learned2d: trained super-stepper")
+    ap.add_argument("--bar", type=float, default=1e-3, help="learned2d: accepted rel. L2 error")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch2d":
         return run_batch(args)
+    if args.workload == "learned2d":
+        return run_learned(args)
     return run_ours(args)
 
 

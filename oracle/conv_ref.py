@@ -9,8 +9,8 @@ reordering:
   y[b, i, j, co] = bias[co] + sum_{ky, kx, ci} x[b, i + (ky-1) d, j + (kx-1) d, ci] w[co, 3 ky + kx, ci]
   (indices mod H and W);
 * its gradients with respect to the input, the weights and the bias;
-* the five-layer network (ReLU after layers 1-4, none after layer 5) and its
-  backward pass, the channel-weighted squared-error loss, and
+* the five-layer network (ReLU after layers 1-4 or no activation at all,
+  none after layer 5) and its backward pass, the channel-weighted squared-error loss, and
 * the bias-corrected Adam update (Kingma and Ba, 2015, Algorithm 1).
 
 It shares nothing with the CUDA library.  These functions are pinned in
@@ -56,14 +56,14 @@ def conv3x3_backward(x, w, dy, dil):
     return dx, dw, db
 
 
-def net_forward(x, params, dils):
+def net_forward(x, params, dils, relu=True):
     """params: list of (w, b) per layer; returns the list of layer outputs
-    [a1, ..., a_L] (ReLU applied to all but the last)."""
+    [a1, ..., a_L] (ReLU applied to all but the last when relu is set)."""
     acts = []
     a = np.asarray(x, dtype=np.float64)
     for li, ((w, b), d) in enumerate(zip(params, dils)):
         z = conv3x3(a, w, b, d)
-        a = np.maximum(z, 0.0) if li + 1 < len(params) else z
+        a = np.maximum(z, 0.0) if (relu and li + 1 < len(params)) else z
         acts.append(a)
     return acts
 
@@ -75,7 +75,7 @@ def weighted_mse(y, t, wch, scale):
     return scale * float(np.sum(wch * e * e)), 2.0 * scale * wch * e
 
 
-def net_backward(x, params, dils, acts, dy_out):
+def net_backward(x, params, dils, acts, dy_out, relu=True):
     """Gradients of sum(dy_out * a_L) with respect to every (w, b)."""
     grads = [None] * len(params)
     dy = np.asarray(dy_out, dtype=np.float64)
@@ -84,7 +84,7 @@ def net_backward(x, params, dils, acts, dy_out):
         dx, dw, db = conv3x3_backward(inp, params[li][0], dy, dils[li])
         grads[li] = (dw, db)
         if li > 0:
-            dy = dx * (acts[li - 1] > 0)  # ReLU derivative of the previous layer
+            dy = dx * (acts[li - 1] > 0) if relu else dx  # ReLU derivative of the previous layer
     return grads
 
 

@@ -57,15 +57,20 @@ class ConvNet:
     """Dilated 3x3 convolution network, NHWC, BF16 storage, FP32 accumulation.
 
     Layers l = 0..L-1 map chans[l] -> chans[l+1] channels with dilation
-    dilations[l]; ReLU after every layer but the last.  Parameters live in one
-    flat FP32 buffer (weights [co][9][ci] then bias [co] per layer) with a
-    BF16 copy that the forward kernels read."""
+    dilations[l]; act = "relu" puts a ReLU after every layer but the last,
+    act = "none" makes the network a composition of linear convolutions.
+    Parameters live in one flat FP32 buffer (weights [co][9][ci] then bias
+    [co] per layer) with a BF16 copy that the forward kernels read."""
 
-    def __init__(self, cin=25, cout=25, width=64, dilations=(1, 2, 4, 8, 1), seed=0):
+    def __init__(self, cin=25, cout=25, width=64, dilations=(1, 2, 4, 8, 1), seed=0, act="relu"):
         import torch
 
         if not (1 <= cin <= CPAD and 1 <= cout <= CPAD):
             raise ValueError("cin and cout must be in 1..32")
+        if act not in ("relu", "none"):
+            raise ValueError("act must be 'relu' or 'none'")
+        self.act = act
+        self.relu = 1 if act == "relu" else 0
         self.dils = tuple(int(d) for d in dilations)
         nl = len(self.dils)
         self.chans = [CPAD] + [int(width)] * (nl - 1) + [CPAD]
@@ -93,14 +98,15 @@ class ConvNet:
 
     # -- parameters ---------------------------------------------------------
     def initial_params(self, seed):
-        """He-normal weights for layers 0..L-2, zero last layer (the residual
-        form starts as the identity map), zero biases, zero padded channels."""
+        """Normal weights with variance 2/fan_in (ReLU) or 1/fan_in (linear)
+        for layers 0..L-2, zero last layer (the residual form starts as the
+        identity map), zero biases, zero padded channels."""
         rng = np.random.default_rng(seed)
         flat = np.zeros(self.nparam, dtype=np.float32)
         for layer, (wo, bo, ci, co) in enumerate(self.layout):
             fan = 9 * (self.cin if layer == 0 else ci)
             if layer + 1 < len(self.layout):
-                w = rng.standard_normal((co, 9, ci)) * math.sqrt(2.0 / fan)
+                w = rng.standard_normal((co, 9, ci)) * math.sqrt((2.0 if self.relu else 1.0) / fan)
                 if layer == 0:
                     w[:, :, self.cin:] = 0.0
             else:
@@ -161,8 +167,8 @@ class ConvNet:
             last = layer + 1 == len(self.layout)
             y16 = None if last else bufs["act"][layer]
             y32 = bufs["out"] if last else None
-            _check(L.hnn_conv3x3_fwd(_p(a), p16 + 2 * wo, p32 + 4 * bo, None, B, H, WIDTH, ci, co, d, 0 if last else 1,
-                                     _p(y16), _p(y32), s), "conv forward")
+            _check(L.hnn_conv3x3_fwd(_p(a), p16 + 2 * wo, p32 + 4 * bo, None, B, H, WIDTH, ci, co, d,
+                                     0 if last else self.relu, _p(y16), _p(y32), s), "conv forward")
             a = y16
         return bufs["out"]
 
@@ -184,8 +190,9 @@ class ConvNet:
             if layer > 0:
                 _check(L.hnn_flip_weights(p16 + 2 * wo, co, ci, _p(self.wt[layer]), s), "flip")
                 nxt = bufs["dy"][layer % 2]
-                _check(L.hnn_conv3x3_fwd(_p(dy), _p(self.wt[layer]), None, _p(acts[layer - 1]), B, H, WIDTH, co, ci, d,
-                                         0, _p(nxt), None, s), "input gradient")
+                mask = acts[layer - 1] if self.relu else None
+                _check(L.hnn_conv3x3_fwd(_p(dy), _p(self.wt[layer]), None, _p(mask), B, H, WIDTH, co, ci, d, 0,
+                                         _p(nxt), None, s), "input gradient")
                 dy = nxt
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -434,7 +441,7 @@ class SuperStepper:
         final_u, final_v = A[0], A[1]
         rej = np.flatnonzero(~acc)
         if len(rej) and fallback:
-            fb = self.fallback_batch(len(rej))
+            fb = self.fallback_batch(len(rej), batch.precision)
             for i, p in enumerate(rej):
                 fb.problem(i).set_state_device(X[0][p], X[1][p])
             fb.step(self.K)
@@ -443,13 +450,15 @@ class SuperStepper:
         self.scatter(batch, final_u, final_v)
         return acc, est
 
-    def fallback_batch(self, n):
+    def fallback_batch(self, n, precision=FP64):
+        """A batch of n problems for the rejected predictions, in the
+        arithmetic of the caller's batch (kept for the next call)."""
         import torch
 
-        if self._fb is None or len(self._fb.problems) != n:
+        if self._fb is None or len(self._fb.problems) != n or self._fb.precision != precision:
             if self._fb is not None:
                 self._fb.close()
-            self._fb = HermiteBatch([self.problem] * n)
+            self._fb = HermiteBatch([self.problem] * n, precision=precision)
             self._fb.set_stream(torch.cuda.current_stream())
         return self._fb
 
@@ -494,14 +503,15 @@ class SuperStepper:
         np.savez(path, params=self.net.get_params(), shift=self.shift.cpu().numpy(), scale=self.scale.cpu().numpy(),
                  dscale=self.dscale.cpu().numpy(), kappa=np.array(np.nan if self.kappa is None else self.kappa),
                  meta=np.array([self.K, self.m, self.N, self.dt / self.h * self.c, self.c]),
-                 dils=np.array(self.net.dils))
+                 dils=np.array(self.net.dils), act=np.array(self.net.act))
 
     @classmethod
     def load(cls, path):
         z = np.load(path)
         K, m, N, lam, c = z["meta"]
+        act = str(z["act"]) if "act" in z.files else "relu"
         net = ConvNet(cin=int((m + 1) ** 2 + m * m), cout=int((m + 1) ** 2 + m * m),
-                      dilations=tuple(int(d) for d in z["dils"]))
+                      dilations=tuple(int(d) for d in z["dils"]), act=act)
         st = cls(K=int(K), m=int(m), N=int(N), lam=float(lam), c=float(c), net=net)
         net.set_params(z["params"])
         st.set_stats(z["shift"], z["scale"], z["dscale"])
@@ -517,35 +527,39 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--act", default="relu", help="comma-separated activations to train, each on the same data")
     ap.add_argument("--calib", type=int, default=256, help="held-out trajectories for the residual calibration")
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--out", required=True, help="output path; with several activations, {act} is replaced")
     a = ap.parse_args(argv)
     import torch
 
     log = lambda s: print(s, flush=True)
-    st = SuperStepper()
+    gen = SuperStepper()
     t0 = time.time()
-    levels = st.generate(range(a.ntraj), nlev=a.nlev, log=log)
+    levels = gen.generate(range(a.ntraj), nlev=a.nlev, log=log)
     log(f"data: {a.ntraj} trajectories x {a.nlev} levels in {time.time() - t0:.1f} s")
-    st.fit_stats(levels)
-    torch.cuda.synchronize()
-    t0 = time.time()
-    st.train(levels, a.iters, batch=a.batch, lr=a.lr, log=log)
-    torch.cuda.synchronize()
-    log(f"training: {a.iters} iterations in {time.time() - t0:.1f} s")
-    del levels
-    e, r = st.calibrate(range(10 ** 6, 10 ** 6 + a.calib))
-    log(f"calibration set: true error median {np.median(e):.3e}, max {e.max():.3e}; "
-        f"error/residual median {np.median(e / r):.3f}, kappa (max) {st.kappa:.3f}")
-    st.save(a.out)
-    log(f"saved {a.out}")
-    e2, r2 = st.evaluate(range(2 * 10 ** 6, 2 * 10 ** 6 + a.calib))
-    est = st.kappa * r2
-    log(f"test set: true error quantiles (10, 50, 90, 100 %) {np.quantile(e2, [0.1, 0.5, 0.9, 1.0])}")
-    for bar in (1e-3, 3e-3, 1e-2, 3e-2, 1e-1):
-        acc = est <= bar
-        log(f"  bar {bar:.0e}: accepted {acc.mean():.3f}, true error <= bar {np.mean(e2 <= bar):.3f}, "
-            f"accepted with true error > bar {np.sum(acc & (e2 > bar))}")
+    gen.fit_stats(levels)
+    for act in a.act.split(","):
+        st = SuperStepper(net=ConvNet(act=act))
+        st.set_stats(gen.shift.cpu().numpy(), gen.scale.cpu().numpy(), gen.dscale.cpu().numpy())
+        torch.cuda.synchronize()
+        t0 = time.time()
+        st.train(levels, a.iters, batch=a.batch, lr=a.lr, log_every=max(1, a.iters // 40), log=log)
+        torch.cuda.synchronize()
+        log(f"[{act}] training: {a.iters} iterations in {time.time() - t0:.1f} s")
+        e, r = st.calibrate(range(10 ** 6, 10 ** 6 + a.calib))
+        log(f"[{act}] calibration set: true error median {np.median(e):.3e}, max {e.max():.3e}; "
+            f"error/residual median {np.median(e / r):.3f}, kappa (max) {st.kappa:.3f}")
+        out = a.out.replace("{act}", act)
+        st.save(out)
+        log(f"[{act}] saved {out}")
+        e2, r2 = st.evaluate(range(2 * 10 ** 6, 2 * 10 ** 6 + a.calib))
+        est = st.kappa * r2
+        log(f"[{act}] test set: true error quantiles (10, 50, 90, 100 %) {np.quantile(e2, [0.1, 0.5, 0.9, 1.0])}")
+        for bar in (1e-3, 3e-3, 1e-2, 3e-2, 1e-1):
+            acc = est <= bar
+            log(f"  bar {bar:.0e}: accepted {acc.mean():.3f}, true error <= bar {np.mean(e2 <= bar):.3f}, "
+                f"accepted with true error > bar {np.sum(acc & (e2 > bar))}")
 
 
 if __name__ == "__main__":

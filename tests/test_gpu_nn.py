@@ -291,7 +291,8 @@ def test_make_pairs_and_moments(hb):
     assert np.allclose(mh[C0:], (d * d).sum(0), rtol=1e-10)
 
 
-def test_network_gradient_against_fp64_reference(hb):
+@pytest.mark.parametrize("act", ["relu", "none"])
+def test_network_gradient_against_fp64_reference(hb, act):
     """Whole network on a tiny batch (1 x 4 x 128): gradients of the kernels
     against the FP64 reference with the kernels' BF16 rounding points
     emulated (activations, loss gradient, input gradients)."""
@@ -300,7 +301,8 @@ def test_network_gradient_against_fp64_reference(hb):
     from paper_1802_05246_b300.learned import CPAD, ConvNet
 
     B, H = 1, 4
-    net = ConvNet(cin=25, cout=25, seed=3)
+    relu = act == "relu"
+    net = ConvNet(cin=25, cout=25, seed=3, act=act)
     rng = _rng(12)
     flat = net.get_params()
     # a nonzero last layer so that every layer receives a gradient
@@ -338,7 +340,7 @@ def test_network_gradient_against_fp64_reference(hb):
     acts, a = [], xh
     for li, ((w, b), d) in enumerate(zip(params, net.dils)):
         z = cr.conv3x3(a, w, b, d)
-        a = r16(np.maximum(z, 0)) if li + 1 < len(params) else z
+        a = r16(np.maximum(z, 0) if relu else z) if li + 1 < len(params) else z
         acts.append(a)
     lref, dy = cr.weighted_mse(acts[-1], tgt, wch, scale)
     assert abs(loss.item() - lref) <= 1e-3 * lref
@@ -349,11 +351,11 @@ def test_network_gradient_against_fp64_reference(hb):
         dx, dw, db = cr.conv3x3_backward(inp, params[li][0], dy, net.dils[li])
         grads[li] = (dw, db)
         if li > 0:
-            dy = r16(dx * (acts[li - 1] > 0))
+            dy = r16(dx * (acts[li - 1] > 0) if relu else dx)
     # and the pure FP64 network (no rounding) for scale
-    acts64 = cr.net_forward(xh, params, net.dils)
+    acts64 = cr.net_forward(xh, params, net.dils, relu)
     _, dy64 = cr.weighted_mse(acts64[-1], tgt, wch, scale)
-    grads64 = cr.net_backward(xh, params, net.dils, acts64, dy64)
+    grads64 = cr.net_backward(xh, params, net.dils, acts64, dy64, relu)
     for li, (wo, bo, ci, co) in enumerate(net.layout):
         gw = G[wo:wo + co * 9 * ci].reshape(co, 9, ci)
         gb = G[bo:bo + co]

@@ -73,7 +73,8 @@ def test_conv_gradients_match_finite_differences(dil):
         assert abs(_fd(lambda a: np.sum(g * cr.conv3x3(x, w, a, dil)), b, (c,)) - db[c]) < 1e-7
 
 
-def test_network_gradients_match_finite_differences():
+@pytest.mark.parametrize("relu", [True, False])
+def test_network_gradients_match_finite_differences(relu):
     dils = (1, 2, 1)
     chans = [3, 4, 4, 2]
     rng = np.random.default_rng(11)
@@ -84,11 +85,11 @@ def test_network_gradients_match_finite_differences():
     wch = np.array([1.0, 0.25])
 
     def loss_of(ps):
-        return cr.weighted_mse(cr.net_forward(x, ps, dils)[-1], t, wch, 0.5)[0]
+        return cr.weighted_mse(cr.net_forward(x, ps, dils, relu)[-1], t, wch, 0.5)[0]
 
-    acts = cr.net_forward(x, params, dils)
+    acts = cr.net_forward(x, params, dils, relu)
     _, dy = cr.weighted_mse(acts[-1], t, wch, 0.5)
-    grads = cr.net_backward(x, params, dils, acts, dy)
+    grads = cr.net_backward(x, params, dils, acts, dy, relu)
     for li in range(3):
         for k in range(6):
             idx = tuple(int(rng.integers(0, n)) for n in params[li][0].shape)
