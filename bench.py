@@ -397,6 +397,78 @@ def run_batch(args):
     return 0
 
 
+# The paper's 3-D performance runs (periodic-type data; "time per iteration"
+# on one P100, FP64), read here as one full step: (variant, m, points per
+# direction, seconds per iteration or None).  Context only, other hardware.
+PAPER_3D_RUNS = [
+    ("simple", 1, 160, 0.057), ("simple", 2, 120, 0.087), ("simple", 3, 90, 0.10),
+    ("full", 1, 160, 0.11), ("full", 2, 120, 0.17), ("full", 3, 90, None),
+    ("conservative", 1, 280, 0.035), ("conservative", 2, 190, 0.052), ("conservative", 3, 140, 0.0579),
+]
+
+
+def run_paper3d(args):
+    """3-D at scale: the paper's own performance configurations (simple and
+    full dissipative, conservative; periodic) and the 128^3 m=3 grid with
+    Dirichlet and Neumann boundaries, FP64 and split precision.  One step =
+    one full time step (two half-steps) of one problem."""
+    import torch
+
+    import paper_1802_05246_b300 as hb
+
+    torch.cuda.set_device(0)
+    vid = {"simple": hb.DISSIPATIVE_SIMPLE, "full": hb.DISSIPATIVE, "conservative": hb.CONSERVATIVE}
+    cases = [(v, m, n, hb.PERIODIC, p100) for (v, m, n, p100) in PAPER_3D_RUNS]
+    cases += [(v, 3, 128, bc, None) for v in ("full", "simple", "conservative")
+              for bc in (hb.PERIODIC, hb.DIRICHLET, hb.NEUMANN)]
+    out = []
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    for (vname, m, n, bc, p100) in cases:
+        # "points per direction": n nodes per axis on the primal grid
+        N = n if bc == hb.PERIODIC else n - 1
+        h = 1.0 / N
+        for prec in (hb.FP64, hb.SPLIT32):
+            g = hb.Hermite(3, m, N, 1.0, h, 0.9 * h, vid[vname], bc, precision=prec)
+            n0 = g.nodes(0)
+            u = torch.randn((n0, g.Nu), dtype=torch.float64, device="cuda", generator=gen)
+            v = torch.randn((n0, g.Nv), dtype=torch.float64, device="cuda", generator=gen) if g.Nv else None
+            g.set_state_device(u, v)
+            del u, v
+            s = torch.cuda.Stream()
+            g.set_stream(s)
+            g.step(args.warmup)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(s)
+            g.step(args.steps)
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            dof = (g.nodes(0) + g.nodes(1)) * (g.Nu + g.Nv)  # DOF-updates of one full step
+            out.append({"variant": vname, "m": m, "points": n, "bc": ["periodic", "dirichlet", "neumann"][bc],
+                        "precision": ["fp64", "split"][prec], "ms_per_full_step": ms,
+                        "dof_updates_per_s": dof / (ms / 1e3),
+                        "p100_s_per_iteration": p100,
+                        "speedup_vs_p100": (p100 * 1e3 / ms) if p100 else None})
+            g.close()
+            torch.cuda.empty_cache()
+    head = next(r for r in out if r["variant"] == "full" and r["m"] == 3 and r["points"] == 128
+                and r["bc"] == "dirichlet" and r["precision"] == "split")
+    line = {
+        "metric": METRIC, "value": head["dof_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_full_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32x2", "data": "synthetic (N(0,1) coefficients; timing does not depend on "
+                                                      "the values)",
+        "config": {"workload": "3-D at scale: the paper's P100 configurations and m=3 128^3 with "
+                               "periodic/Dirichlet/Neumann boundaries, c*dt/h=0.9",
+                   "step": "one full time step of one problem", "headline": "full dissipative, m=3, 128^3, "
+                                                                            "Dirichlet, split"},
+        "cases": out,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1802_05246_b300", "weights", "superstepper_k16.npz")
 
 
@@ -507,7 +579,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid3d", choices=["grid3d", "batch2d", "learned2d"])
+    ap.add_argument("--workload", default="grid3d", choices=["grid3d", "batch2d", "learned2d", "paper3d"])
     ap.add_argument("--weights", default=LEARNED_WEIGHTS, help="learned2d: trained super-stepper")
     ap.add_argument("--bar", type=float, default=1e-3, help="learned2d: accepted rel. L2 error")
     args = ap.parse_args()
@@ -517,6 +589,8 @@ def main():
         return run_batch(args)
     if args.workload == "learned2d":
         return run_learned(args)
+    if args.workload == "paper3d":
+        return run_paper3d(args)
     return run_ours(args)
 
 

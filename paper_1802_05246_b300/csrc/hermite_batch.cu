@@ -325,7 +325,7 @@ void free_items(hermite_batch *b) {
 
 int group_key(const hermite_batch *b, const hermite_ctx *ctx) {
   if (b->precision == HERMITE_SPLIT32) return ctx->nomax;
-  return ctx->nco <= 16 ? 16 : (ctx->nco <= 32 ? 32 : 48);
+  return ctx->nco <= 8 ? 8 : (ctx->nco <= 16 ? 16 : (ctx->nco <= 32 ? 32 : 48));
 }
 
 int build_items(hermite_batch *b) {
@@ -413,13 +413,18 @@ template <int D>
 int launch_group(hermite_batch *b, int k, const hermite_batch::Group &gr, unsigned *counter) {
   const unsigned blocks = (unsigned)(b->nsm * b->blocks_per_sm);
   if (b->precision == HERMITE_SPLIT32) {
+    // the template must equal the contexts' slot count: it is the stride of their split operators
     switch (gr.tmpl) {
+      case 2: batch_split_kernel<D, 2><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 4: batch_split_kernel<D, 4><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       case 8: batch_split_kernel<D, 8><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       case 16: batch_split_kernel<D, 16><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      default: batch_split_kernel<D, 32><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 32: batch_split_kernel<D, 32><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      default: return HERMITE_ERR_ARG;
     }
   } else {
     switch (gr.tmpl) {
+      case 8: batch_f64_kernel<D, 8><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       case 16: batch_f64_kernel<D, 16><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       case 32: batch_f64_kernel<D, 32><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       default: batch_f64_kernel<D, 48><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;

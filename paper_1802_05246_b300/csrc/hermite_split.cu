@@ -241,9 +241,14 @@ int launch_split_dn(hermite_ctx *ctx, const Geometry &g, const float2 *src, floa
 
 template <int D>
 int launch_split_d(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub) {
-  if (ctx->nomax <= 8) return launch_split_dn<D, 8>(ctx, g, src, dst, sub);
-  if (ctx->nomax <= 16) return launch_split_dn<D, 16>(ctx, g, src, dst, sub);
-  return launch_split_dn<D, 32>(ctx, g, src, dst, sub);
+  switch (ctx->nomax) {
+    case 2: return launch_split_dn<D, 2>(ctx, g, src, dst, sub);
+    case 4: return launch_split_dn<D, 4>(ctx, g, src, dst, sub);
+    case 8: return launch_split_dn<D, 8>(ctx, g, src, dst, sub);
+    case 16: return launch_split_dn<D, 16>(ctx, g, src, dst, sub);
+    case 32: return launch_split_dn<D, 32>(ctx, g, src, dst, sub);
+  }
+  return HERMITE_ERR_ARG;
 }
 
 // Energy forms on split-precision levels: the factored form of the FP64
@@ -462,7 +467,8 @@ int build_split_operator(hermite_ctx *ctx) {
   for (int r = 0; r < ctx->nco; ++r) counts[parh[r]]++;
   int nomax = 0;
   for (int c = 0; c < nclass; ++c) nomax = std::max(nomax, counts[c]);
-  ctx->nomax = nomax <= 8 ? 8 : (nomax <= 16 ? 16 : 32);
+  // slots per class warp: the smallest even count that holds the largest class
+  ctx->nomax = nomax <= 2 ? 2 : (nomax <= 4 ? 4 : (nomax <= 8 ? 8 : (nomax <= 16 ? 16 : 32)));
   if (nomax > 32) return HERMITE_ERR_UNSUPPORTED;
   std::vector<int16_t> outrow((size_t)nclass * ctx->nomax, -1);
   std::vector<int8_t> npc(nclass, 0);

@@ -166,6 +166,7 @@ int launch_dch(hermite_ctx *ctx, const Geometry &g, const double *M, int nci, in
 template <int D>
 int launch_d(hermite_ctx *ctx, const Geometry &g, const double *M, int nci, int nco, const double *src,
              double *dst, bool sub) {
+  if (nco <= 8) return launch_dch<D, 8>(ctx, g, M, nci, nco, src, dst, sub);
   if (nco <= 16) return launch_dch<D, 16>(ctx, g, M, nci, nco, src, dst, sub);
   if (nco <= 32) return launch_dch<D, 32>(ctx, g, M, nci, nco, src, dst, sub);
   if (nco <= 64) return launch_dch<D, 64>(ctx, g, M, nci, nco, src, dst, sub);

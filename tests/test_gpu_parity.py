@@ -276,6 +276,66 @@ def test_full_size_3d_sampled(hb, orc, variant):
     assert rel_l2(np.concatenate([pu[t], pv[t]], 1), np.concatenate([wu, wv], 1)) <= TOL
 
 
+def _boundary_targets(rng, n, count):
+    """Random node indices of an n^3 grid plus every corner and some face and
+    edge nodes (where the ghost polynomials enter)."""
+    idx = [rng.integers(0, n ** 3, count)]
+    ends = [0, n - 1]
+    idx.append(np.array([(i * n + j) * n + k for i in ends for j in ends for k in ends]))
+    f = rng.integers(0, n, (3, 40))
+    for ax in range(3):
+        c = f.copy()
+        c[ax] = rng.choice(ends, 40)
+        idx.append((c[0] * n + c[1]) * n + c[2])
+    return np.concatenate(idx)
+
+
+_BC_DATA = {}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("bc", [1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_full_size_3d_boundaries_sampled(hb, orc, variant, bc, precision):
+    """3-D m=3, 96^3 cells (97^3 primal nodes) with Dirichlet or Neumann
+    boundaries, every variant, FP64 and split: two half-steps from seeded odd
+    or even Gaussian-pulse data, sampled targets (all corners, faces, edges)
+    recomputed by the oracle from the GPU's input level."""
+    d, m, N = 3, 3, 96
+    h = 1.0 / N
+    g = hb.Hermite(d, m, N, 1.0, h, 0.9 * h, variant, bc, precision=precision)
+    P = orc.Problem(d, m, N, 1.0, h, 0.9 * h, variant, bc)
+    if (N, bc) not in _BC_DATA:
+        cen, wid, amp = I.pulses_3d_config(1)
+        _BC_DATA[(N, bc)] = I.gaussian_data(d, m, N, h, bc, 0, cen, wid, amp)
+    u0 = _BC_DATA[(N, bc)]
+    n0 = g.nodes(0)
+    v0 = np.zeros((n0, m ** 3))
+    g.set_state(u0, v0)
+    rng = np.random.default_rng(21 + bc)
+    tol = TOL if precision == 0 else 1e-9
+    assert n0 == (N + 1) ** 3 and g.nodes(1) == N ** 3  # primal N+1, dual N nodes per axis
+    t1 = _boundary_targets(rng, N, 300)
+    t0 = _boundary_targets(rng, N + 1, 300)
+    if variant == orc.CONSERVATIVE:
+        q0, _ = g.get_grid(1)
+        g.advance_half(1)
+        p1, _ = g.get_grid(0)
+        assert rel_l2(p1[t0], P.half_step_sample(0, q0, None, t0, old_u=u0[t0])) <= tol
+        g.advance_half(1)
+        q1, _ = g.get_grid(1)
+        assert rel_l2(q1[t1], P.half_step_sample(1, p1, None, t1, old_u=q0[t1])) <= tol
+        return
+    g.advance_half(1)
+    du, dv = g.get_grid(1)
+    wu, wv = P.half_step_sample(1, u0, v0, t1)
+    assert rel_l2(np.concatenate([du[t1], dv[t1]], 1), np.concatenate([wu, wv], 1)) <= tol
+    g.advance_half(1)
+    pu, pv = g.get_grid(0)
+    wu, wv = P.half_step_sample(0, du, dv, t0)
+    assert rel_l2(np.concatenate([pu[t0], pv[t0]], 1), np.concatenate([wu, wv], 1)) <= tol
+
+
 @pytest.mark.parametrize("variant", [0, 1])
 def test_full_size_2d_sampled(hb, orc, variant):
     """2-D periodic m=4, 256^2, lambda = 1, u0 = sin 2pi x sin 2pi y: 8 steps on

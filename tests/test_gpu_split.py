@@ -26,6 +26,8 @@ def hb():
     (1, 3, 16, 0.9, 0, 0, 10), (1, 3, 16, 0.9, 1, 0, 10), (2, 4, 10, 1.0, 0, 0, 4), (2, 4, 10, 1.0, 1, 0, 4),
     (2, 2, 7, 0.8, 2, 1, 3), (3, 3, 5, 0.9, 0, 0, 2), (3, 3, 5, 0.9, 1, 0, 2), (3, 1, 6, 0.9, 0, 2, 3),
     (2, 6, 5, 0.8, 0, 0, 2), (1, 6, 9, 0.7, 1, 1, 6),
+    # small operators (two or four slots per class warp)
+    (3, 1, 5, 0.9, 1, 0, 2), (3, 1, 4, 1.0, 2, 1, 2), (2, 1, 6, 0.9, 1, 2, 3), (1, 1, 9, 1.0, 0, 0, 5),
 ])
 def test_split_matches_oracle(hb, orc, d, m, N, lam, variant, bc, nsteps):
     h = 1.0 / N
