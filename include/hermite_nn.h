@@ -47,6 +47,24 @@ extern "C" {
 int hnn_conv3x3_fwd(const uint16_t *x, const uint16_t *w, const float *bias, const uint16_t *mask, int B, int H,
                     int W, int Cin, int Cout, int dil, int relu, uint16_t *y_bf16, float *y_f32, void *stream);
 
+/* Engine of hnn_conv3x3_fwd (process-wide): 0 (default) runs Cin = 64 layers
+ * with dilation <= 8 on the fifth-generation tensor cores (tcgen05 MMAs with
+ * tensor-memory accumulators, TMA-loaded input rows; other layers stay on
+ * mma.sync),
+ * 1 runs every layer on the mma.sync kernels.  Returns HERMITE_ERR_ARG for
+ * another value. */
+int hnn_set_conv_engine(int engine);
+
+/* Synchronises the device, then returns HERMITE_ERR_TIMEOUT (and clears the
+ * flag) if a tensor-core convolution gave up a bounded wait since the last
+ * call (its output is then incomplete), else HERMITE_OK. */
+int hnn_conv_status(void);
+
+/* Self-test of the tensor-core path on one CTA: D[128][N] = A[128][64] B[N][64]^T,
+ * A and B BF16 row-major, D FP32 row-major, N = 32 or 64; *status (device int,
+ * caller-initialised to 0) is set to 1 if the MMA completion wait ran out. */
+int hnn_tc_gemm_selftest(const uint16_t *A, const uint16_t *B, float *D, int N, int *status, void *stream);
+
 /* Weights of the input-gradient convolution: wt[ci][tap][co] = w[co][8-tap][ci].
  * The gradient with respect to a layer's input is then
  * hnn_conv3x3_fwd(dy, wt, NULL, mask, ..., Cin = layer Cout, Cout = layer Cin). */

@@ -37,6 +37,7 @@ EXPORTS = [
     # include/hermite_nn.h
     "hnn_conv3x3_fwd", "hnn_flip_weights", "hnn_conv3x3_wgrad", "hnn_bias_grad", "hnn_mse", "hnn_adam",
     "hnn_state_to_f32", "hnn_pack_state", "hnn_unpack_state", "hnn_make_pairs", "hnn_moments", "hnn_sqdiff",
+    "hnn_set_conv_engine", "hnn_conv_status", "hnn_tc_gemm_selftest",
 ]
 
 
@@ -103,6 +104,9 @@ def lib():
         "hnn_make_pairs": (c_int, [vp, vp, vp, c_int, i64, c_int, vp, vp, vp, c_int, vp, vp, vp]),
         "hnn_moments": (c_int, [vp, vp, i64, c_int, vp, vp]),
         "hnn_sqdiff": (c_int, [vp, vp, vp, vp, i64, c_int, c_int, c_dbl, vp, vp]),
+        "hnn_set_conv_engine": (c_int, [c_int]),
+        "hnn_conv_status": (c_int, []),
+        "hnn_tc_gemm_selftest": (c_int, [vp, vp, vp, c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -26,6 +26,7 @@
 
 #include "hermite.h"
 #include "hermite_nn.h"
+#include "hermite_nn_internal.h"
 
 namespace hermite_nn {
 namespace {
@@ -606,6 +607,7 @@ int hnn_conv3x3_fwd(const uint16_t *x, const uint16_t *w, const float *bias, con
   auto M = reinterpret_cast<const bf16 *>(mask);
   auto Y = reinterpret_cast<bf16 *>(y_bf16);
   cudaStream_t s = as_stream(stream);
+  if (tc_conv_supported(Cin, Cout, dil)) return tc_conv_fwd(X, Wt, bias, M, rows, H, dil, relu, Y, y_f32, Cout, s);
   if (Cin == 32 && Cout == 64) return launch_fwd<32, 64>(X, Wt, bias, M, rows, H, dil, relu, Y, y_f32, s);
   if (Cin == 64 && Cout == 64) return launch_fwd<64, 64>(X, Wt, bias, M, rows, H, dil, relu, Y, y_f32, s);
   if (Cin == 64 && Cout == 32) return launch_fwd<64, 32>(X, Wt, bias, M, rows, H, dil, relu, Y, y_f32, s);

@@ -61,10 +61,42 @@ def _conv_abs(x, w, b, dil):
     return cr.conv3x3(np.abs(x), np.abs(w), None if b is None else np.abs(b), dil)
 
 
+@pytest.fixture
+def engine(hb, request):
+    """Selects the convolution engine for one test (0: tcgen05 where supported,
+    1: mma.sync) and checks afterwards that no tensor-core wait ran out."""
+    L = hb.lib()
+    assert L.hnn_set_conv_engine(request.param) == 0
+    yield request.param
+    assert L.hnn_set_conv_engine(0) == 0
+    assert L.hnn_conv_status() == 0
+
+
+@pytest.mark.parametrize("N", [64, 32])
+def test_tensor_core_selftest_gemm(hb, N):
+    """One 128 x N x 64 tile through tcgen05 (shared-memory descriptors,
+    instruction descriptor, tensor-memory accumulator and load) against FP64."""
+    import torch
+
+    rng = _rng(40 + N)
+    A, Ah = _bf(rng.standard_normal((128, 64)))
+    B, Bh = _bf(rng.standard_normal((N, 64)))
+    D = torch.full((128, N), float("nan"), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert hb.lib().hnn_tc_gemm_selftest(A.data_ptr(), B.data_ptr(), D.data_ptr(), N, st.data_ptr(), _stream()) == 0
+    got = _host(D)
+    assert int(st.item()) == 0
+    ref = Ah @ Bh.T
+    S = np.abs(Ah) @ np.abs(Bh).T
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ref) / S) <= 1e-4
+
+
+@pytest.mark.parametrize("engine", [0, 1], indirect=True)
 @pytest.mark.parametrize("cin,cout", [(32, 64), (64, 64), (64, 32), (32, 32)])
-@pytest.mark.parametrize("dil", [1, 3, 8])
+@pytest.mark.parametrize("dil", [1, 3, 8, 12])
 @pytest.mark.parametrize("relu", [0, 1])
-def test_conv_forward(hb, cin, cout, dil, relu):
+def test_conv_forward(hb, engine, cin, cout, dil, relu):
     import torch
 
     B, H = 2, 5  # H < 2*dil: the row offsets wrap around more than once
@@ -89,9 +121,10 @@ def test_conv_forward(hb, cin, cout, dil, relu):
     assert np.all(np.abs(g16 - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-4 * S)
 
 
+@pytest.mark.parametrize("engine", [0, 1], indirect=True)
 @pytest.mark.parametrize("cin,cout", [(32, 64), (64, 64), (64, 32)])
 @pytest.mark.parametrize("dil", [1, 2, 4, 8])
-def test_input_gradient_via_flipped_weights_and_mask(hb, cin, cout, dil):
+def test_input_gradient_via_flipped_weights_and_mask(hb, engine, cin, cout, dil):
     import torch
 
     B, H = 2, 6
@@ -138,7 +171,8 @@ def test_weight_and_bias_gradients_accumulate(hb, cin, cout, dil):
     assert np.max(np.abs(got_b - (db0 + gb)) / (Sb + np.abs(db0))) <= 1e-4
 
 
-def test_full_size_forward_and_weight_gradient_sampled(hb):
+@pytest.mark.parametrize("engine", [0, 1], indirect=True)
+def test_full_size_forward_and_weight_gradient_sampled(hb, engine):
     """The launch configuration of training and inference (32 images of
     128 x 128, 64 -> 64 channels, dilation 8): sampled outputs and weight
     gradient entries computed one by one in FP64."""
