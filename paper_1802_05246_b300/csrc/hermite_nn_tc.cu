@@ -7,10 +7,9 @@
 // swizzle) in a four-stage ring.  The column shift of the taps is moved to
 // the output: for each kernel column kx an accumulator in tensor memory
 // collects D_kx[q] = sum_ky X_ky[q] W_{ky,kx}^T, and the epilogue forms
-// y[p] = D_0[p - dil] + D_1[p] + D_2[p + dil] (indices mod 128): the shifted
-// accumulator rows move between lanes with warp shuffles, and only the dil
-// rows that cross a 32-row quarter of tensor memory go through shared memory
-// (dilations up to 8; larger ones use the mma.sync kernel).  A shifted operand tile
+// y[p] = D_0[p - dil] + D_1[p] + D_2[p + dil] (indices mod 128), exchanging
+// D_0 and D_2 through shared memory with 16-byte accesses (dilations up to 8;
+// larger ones use the mma.sync kernel).  A shifted operand tile
 // cannot be described by a tensor-core shared-memory descriptor (its rows
 // would not start on the 8-row swizzle atoms), an output shift needs no copy.
 //
@@ -268,13 +267,13 @@ __global__ void __launch_bounds__(128) tc_gemm_selftest_kernel(const bf16 *__res
 // ---------------------------------------------------------------------------
 template <int COUT>
 struct TcCfg {
-  static constexpr int STAGES = 8;
+  static constexpr int STAGES = COUT == 64 ? 5 : 8;
   static constexpr int A_BYTES = 128 * 128;            // one input row: 128 nodes x 64 channels BF16
   static constexpr int W_BYTES = 9 * COUT * 128;       // [tap][co] rows of 64 BF16
   static constexpr int CH = COUT / 2;                  // channels per epilogue thread
-  static constexpr int PLD = CH + 1;                   // boundary-row stride in floats (conflict-free)
-  // boundary rows of D_0 and D_2: [2][lane quarter][channel half][kMaxTcDil rows][PLD]
-  static constexpr int X_BYTES = 2 * 4 * 2 * kMaxTcDil * PLD * 4;
+  static constexpr int XLD = COUT + 4;                 // exchange row stride in floats: 16-byte accesses
+                                                       // of 8 consecutive rows hit distinct banks
+  static constexpr int X_BYTES = 2 * 128 * XLD * 4;    // D_0 and D_2 of all 128 rows
   static constexpr int ACC = 3 * COUT;                 // tensor-memory columns of one accumulator set
   static constexpr uint32_t TMEM_COLS = 2 * ACC <= 256 ? 256 : 512;
   static constexpr size_t SMEM = 1024 + W_BYTES + STAGES * A_BYTES + X_BYTES + 256;
@@ -403,10 +402,7 @@ __global__ void __launch_bounds__(320, 1)
     const int q = warp & 3, half = (warp - 2) >> 2;
     const int p = q * 32 + lane;     // output node of this thread
     const int cb = half * C::CH;     // first channel of this thread
-    // pub0[q][half][i]: D_0 of lane 32 - dil + i of quarter q (read by quarter q + 1);
-    // pub2[q][half][i]: D_2 of lane i of quarter q (read by quarter q - 1)
-    float *pub0 = xch, *pub2 = xch + 4 * 2 * kMaxTcDil * C::PLD;
-    auto row_of = [&](float *pub, int qq, int i) { return pub + ((qq * 2 + half) * kMaxTcDil + i) * C::PLD; };
+    float *x0 = xch, *x2 = xch + 128 * C::XLD;
     float bz[C::CH];  // this thread's biases, loaded once
 #pragma unroll
     for (int j = 0; j < C::CH; ++j) bz[j] = bias ? bias[cb + j] : 0.f;
@@ -415,7 +411,9 @@ __global__ void __launch_bounds__(320, 1)
       const int a = ri & 1, use = ri >> 1;
       const bool ok = mbar_wait(tfull + a, use & 1);
       if (!ok) atomicExch(&s_err, 1);
-      if (named_sync_or(1, C::EPI, !ok || read_flag(&s_err))) break;  // all epilogue warps leave together
+      // all epilogue warps leave together; this barrier also orders the previous
+      // row's exchange reads before this row's exchange writes
+      if (named_sync_or(1, C::EPI, !ok || read_flag(&s_err))) break;
       tc_fence_after();
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * C::ACC + cb);
       float acc[C::CH], d0[C::CH], d2[C::CH];
@@ -428,28 +426,23 @@ __global__ void __launch_bounds__(320, 1)
       }
       tc_fence_before();
       mbar_arrive(tempty + a);
-      if (lane >= 32 - dil) {
-        float *o0 = row_of(pub0, q, lane - (32 - dil));
 #pragma unroll
-        for (int j = 0; j < C::CH; ++j) o0[j] = d0[j];
-      }
-      if (lane < dil) {
-        float *o2 = row_of(pub2, q, lane);
-#pragma unroll
-        for (int j = 0; j < C::CH; ++j) o2[j] = d2[j];
+      for (int j = 0; j < C::CH; j += 4) {
+        *reinterpret_cast<float4 *>(x0 + p * C::XLD + cb + j) = make_float4(d0[j], d0[j + 1], d0[j + 2], d0[j + 3]);
+        *reinterpret_cast<float4 *>(x2 + p * C::XLD + cb + j) = make_float4(d2[j], d2[j + 1], d2[j + 2], d2[j + 3]);
       }
       named_sync(1, C::EPI);
-      const float *i0 = row_of(pub0, (q + 3) & 3, lane < dil ? lane : 0);
-      const float *i2 = row_of(pub2, (q + 1) & 3, lane + dil >= 32 ? lane + dil - 32 : 0);
+      const float *r0 = x0 + ((p - dil) & 127) * C::XLD + cb;
+      const float *r2 = x2 + ((p + dil) & 127) * C::XLD + cb;
 #pragma unroll
-      for (int j = 0; j < C::CH; ++j) {
-        float s0 = __shfl_up_sync(0xffffffffu, d0[j], dil);    // D_0 of lane - dil
-        float s2 = __shfl_down_sync(0xffffffffu, d2[j], dil);  // D_2 of lane + dil
-        if (lane < dil) s0 = i0[j];
-        if (lane + dil >= 32) s2 = i2[j];
-        acc[j] += s0 + s2;
+      for (int j = 0; j < C::CH; j += 4) {
+        const float4 u = *reinterpret_cast<const float4 *>(r0 + j);
+        const float4 v = *reinterpret_cast<const float4 *>(r2 + j);
+        acc[j] += u.x + v.x;
+        acc[j + 1] += u.y + v.y;
+        acc[j + 2] += u.z + v.z;
+        acc[j + 3] += u.w + v.w;
       }
-      named_sync(1, C::EPI);  // the boundary rows are rewritten for the next row
       const size_t o = ((size_t)r * 128 + p) * COUT + cb;
 #pragma unroll
       for (int j = 0; j < C::CH; j += 8) {
