@@ -231,6 +231,18 @@ int hermite_batch_set_stream(hermite_batch *b, void *stream);
 /* Advance every problem by nsteps full steps (device work only). */
 int hermite_batch_step(hermite_batch *b, int64_t nsteps);
 
+/* Every problem's level on `grid` in one launch on the batch stream (no
+ * synchronisation): u receives the [nodes][Nu] host-layout blocks of problems
+ * 0, 1, ... back to back, v the [nodes][Nv] blocks (v may be NULL; nothing is
+ * written to it for conservative problems).  Device pointers. */
+int hermite_batch_get_states_device(hermite_batch *b, int grid, double *u, double *v);
+
+/* Inverse for the primal level of dissipative problems (the state, as
+ * hermite_set_state_device on each problem: clocks restart at 0); same
+ * back-to-back layout, v may be NULL (= 0).  HERMITE_ERR_STATE if a problem is
+ * conservative (its start-up level needs hermite_set_state). */
+int hermite_batch_set_states_device(hermite_batch *b, const double *u, const double *v);
+
 /* DOF-updates of one full step of the whole batch (both half-steps). */
 int64_t hermite_batch_dof_per_step(const hermite_batch *b);
 

@@ -96,22 +96,25 @@ int hnn_adam(float *p, float *g, float *m, float *v, int64_t n, float lr, float 
 int hnn_state_to_f32(const double *u, const double *v, int64_t n, int Nu, int Nv, double vscale, float *out, int ld,
                      void *stream);
 
-/* Network input of one problem: x[i][c] = bf16((s_c - shift[c]) / scale[c])
- * for the metric-space value s_c of node i, c < Nu+Nv, and 0 for
- * Nu+Nv <= c < C. */
+/* Network input of n nodes (one problem, or several back to back):
+ * x[i][c] = bf16((s_c - shift[c]) / scale[c]) for the metric-space value s_c of
+ * node i, c < Nu+Nv <= 64, and 0 for Nu+Nv <= c < C.  Evaluated in FP32 as
+ * (fl32(s_c) - fl32(shift[c])) * fl32(1 / scale[c]), with
+ * fl32(s_c) = fl32(v) * fl32(vscale) for the v channels. */
 int hnn_pack_state(const double *u, const double *v, int64_t n, int Nu, int Nv, double vscale, const double *shift,
                    const double *scale, int C, uint16_t *x, void *stream);
 
-/* Residual update of one problem: u_out = u + dscale[c] y[i][c] and
- * v_out = v + dscale[c] y[i][c] / vscale (FP64; the outputs may alias the
- * inputs); y FP32 [n][C]. */
+/* Residual update of n nodes: with the change d = fl32(fl32(dscale[c]) y[i][c])
+ * (FP32), u_out = u + d and v_out = v + d / vscale (FP64; the outputs may
+ * alias the inputs); y FP32 [n][C], Nu+Nv <= 64. */
 int hnn_unpack_state(const double *u, const double *v, const float *y, int64_t n, int Nu, int Nv, double vscale,
                      const double *dscale, int C, double *u_out, double *v_out, void *stream);
 
-/* Training pairs from stored metric-space levels (FP32 rows of C0 channels):
- * for sample s, a = levels + src[s], b = levels + dst[s] (element offsets,
- * n rows each): x[s][i][c] = bf16((a - shift[c]) / scale[c]) and
- * t[s][i][c] = (b - a) / dscale[c] for c < C0, zeros up to C. */
+/* Training pairs from stored metric-space levels (FP32 rows of C0 <= 64
+ * channels): for sample s, a = levels + src[s], b = levels + dst[s] (element
+ * offsets, n rows each): x[s][i][c] = bf16((a - shift[c]) / scale[c]) and
+ * t[s][i][c] = (b - a) / dscale[c] for c < C0, zeros up to C (FP32 arithmetic
+ * with the reciprocals rounded to FP32). */
 int hnn_make_pairs(const float *levels, const int64_t *src, const int64_t *dst, int nsamp, int64_t n, int C0,
                    const double *shift, const double *scale, const double *dscale, int C, uint16_t *x, float *t,
                    void *stream);
@@ -125,6 +128,16 @@ int hnn_moments(const float *a, const float *b, int64_t n, int C, double *out, v
  * be NULL when Nv = 0. */
 int hnn_sqdiff(const double *a_u, const double *a_v, const double *b_u, const double *b_v, int64_t n, int Nu, int Nv,
                double vscale, double *out, void *stream);
+
+/* hnn_sqdiff for nsamp problems at once: a_u, b_u [nsamp][n][Nu], a_v, b_v
+ * [nsamp][n][Nv] back to back; out[2 s], out[2 s + 1] += the sums of sample s. */
+int hnn_sqdiff_batch(const double *a_u, const double *a_v, const double *b_u, const double *b_v, int nsamp, int64_t n,
+                     int Nu, int Nv, double vscale, double *out, void *stream);
+
+/* Block copy: dst[didx[i]] = src[sidx[i]] for i < nblk, blocks of `block`
+ * doubles (sidx or didx NULL: the identity); index arrays are device int64. */
+int hnn_copy_blocks(const double *src, const int64_t *sidx, double *dst, const int64_t *didx, int nblk, int64_t block,
+                    void *stream);
 
 #ifdef __cplusplus
 }

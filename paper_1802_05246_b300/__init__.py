@@ -33,11 +33,12 @@ EXPORTS = [
     "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error", "hermite_energy_noalloc",
     "hermite_create_ex", "hermite_batch_create", "hermite_batch_destroy", "hermite_batch_problem",
     "hermite_batch_set_stream", "hermite_batch_step", "hermite_batch_dof_per_step", "hermite_batch_autotune",
-    "hermite_batch_config", "hermite_batch_last_error",
+    "hermite_batch_config", "hermite_batch_last_error", "hermite_batch_get_states_device",
+    "hermite_batch_set_states_device",
     # include/hermite_nn.h
     "hnn_conv3x3_fwd", "hnn_flip_weights", "hnn_conv3x3_wgrad", "hnn_bias_grad", "hnn_mse", "hnn_adam",
     "hnn_state_to_f32", "hnn_pack_state", "hnn_unpack_state", "hnn_make_pairs", "hnn_moments", "hnn_sqdiff",
-    "hnn_set_conv_engine", "hnn_conv_status", "hnn_tc_gemm_selftest",
+    "hnn_set_conv_engine", "hnn_conv_status", "hnn_tc_gemm_selftest", "hnn_sqdiff_batch", "hnn_copy_blocks",
 ]
 
 
@@ -91,6 +92,8 @@ def lib():
         "hermite_batch_autotune": (c_int, [vp, ip, ip, dp]),
         "hermite_batch_config": (c_int, [vp, c_int, c_int]),
         "hermite_batch_last_error": (ctypes.c_char_p, [vp]),
+        "hermite_batch_get_states_device": (c_int, [vp, c_int, vp, vp]),
+        "hermite_batch_set_states_device": (c_int, [vp, vp, vp]),
         "hnn_conv3x3_fwd": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, c_int, c_int, c_int, c_int, vp, vp, vp]),
         "hnn_flip_weights": (c_int, [vp, c_int, c_int, vp, vp]),
         "hnn_conv3x3_wgrad": (c_int, [vp, vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, vp]),
@@ -107,6 +110,8 @@ def lib():
         "hnn_set_conv_engine": (c_int, [c_int]),
         "hnn_conv_status": (c_int, []),
         "hnn_tc_gemm_selftest": (c_int, [vp, vp, vp, c_int, vp, vp]),
+        "hnn_sqdiff_batch": (c_int, [vp, vp, vp, vp, c_int, i64, c_int, c_int, c_dbl, vp, vp]),
+        "hnn_copy_blocks": (c_int, [vp, vp, vp, vp, c_int, i64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -298,6 +303,14 @@ class HermiteBatch:
 
     def config(self, item_nodes, blocks_per_sm):
         self._check(lib().hermite_batch_config(self._b, int(item_nodes), int(blocks_per_sm)))
+
+    def get_states_device(self, grid, u, v=None):
+        """All problems' levels on `grid` into device buffers, back to back."""
+        self._check(lib().hermite_batch_get_states_device(self._b, int(grid), _ptr(u), _ptr(v)))
+
+    def set_states_device(self, u, v=None):
+        """All (dissipative) problems' states from device buffers, back to back."""
+        self._check(lib().hermite_batch_set_states_device(self._b, _ptr(u), _ptr(v)))
 
     def close(self):
         if getattr(self, "_b", None):

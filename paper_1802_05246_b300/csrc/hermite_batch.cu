@@ -293,6 +293,7 @@ struct hermite_batch {
   int item_nodes = 1024, blocks_per_sm = 2, nsm = 148;
   cudaGraphExec_t graph = nullptr;
   int64_t half = 0;
+  void *d_state[2] = {nullptr, nullptr};  // per-grid StateDesc arrays of the batched state transfers
   std::string err;
 };
 
@@ -451,6 +452,79 @@ int enqueue_half(hermite_batch *b, int k) {
   return HERMITE_OK;
 }
 
+// Batched state transfer: every problem's level, host layout [node][coef],
+// problems back to back in one device buffer (u and v separately).
+struct StateDesc {
+  double *g;      // FP64 SoA grid [ncoef][ld]
+  float2 *fg;     // split SoA grid (NULL for FP64 contexts)
+  int64_t ld, nodes, off_u, off_v;
+  int Nu, Nv;     // Nv = 0 for the conservative method
+};
+
+__global__ void batch_get_states_kernel(const StateDesc *__restrict__ d, double *__restrict__ u,
+                                        double *__restrict__ v) {
+  const StateDesc D = d[blockIdx.y];
+  const int nc = D.Nu + D.Nv;
+  const int64_t total = D.nodes * nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = e / nc;
+    const int c = (int)(e % nc);
+    const int64_t i = (int64_t)c * D.ld + node;
+    const double val = D.fg ? (double)D.fg[i].x + (double)D.fg[i].y : D.g[i];
+    if (c < D.Nu)
+      u[D.off_u + node * D.Nu + c] = val;
+    else if (v)
+      v[D.off_v + node * D.Nv + (c - D.Nu)] = val;
+  }
+}
+
+__global__ void batch_set_states_kernel(const StateDesc *__restrict__ d, const double *__restrict__ u,
+                                        const double *__restrict__ v) {
+  const StateDesc D = d[blockIdx.y];
+  const int nc = D.Nu + D.Nv;
+  const int64_t total = D.nodes * nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = e / nc;
+    const int c = (int)(e % nc);
+    const int64_t i = (int64_t)c * D.ld + node;
+    const double val = c < D.Nu ? u[D.off_u + node * D.Nu + c] : (v ? v[D.off_v + node * D.Nv + (c - D.Nu)] : 0.0);
+    D.g[i] = val;
+    if (D.fg) {
+      const float hi = __double2float_rn(val);
+      D.fg[i] = make_float2(hi, __double2float_rn(val - (double)hi));
+    }
+  }
+}
+
+int state_descs(hermite_batch *b, int grid, const StateDesc **out, int64_t *max_elems) {
+  int64_t ou = 0, ov = 0, mx = 0;
+  std::vector<StateDesc> h(b->nprob);
+  for (int p = 0; p < b->nprob; ++p) {
+    hermite_ctx *c = b->probs[p];
+    StateDesc &D = h[p];
+    D.g = c->grid[grid];
+    D.fg = c->precision == HERMITE_SPLIT32 ? c->fgrid[grid] : nullptr;
+    D.ld = c->ld[grid];
+    D.nodes = c->nodes[grid];
+    D.Nu = c->Nu;
+    D.Nv = c->variant == HERMITE_CONSERVATIVE ? 0 : c->Nv;
+    D.off_u = ou;
+    D.off_v = ov;
+    ou += D.nodes * D.Nu;
+    ov += D.nodes * D.Nv;
+    mx = std::max<int64_t>(mx, D.nodes * (D.Nu + D.Nv));
+  }
+  if (!b->d_state[grid]) {
+    if (!bok(b, cudaMalloc(&b->d_state[grid], sizeof(StateDesc) * b->nprob), "cudaMalloc state descs") ||
+        !bok(b, cudaMemcpy(b->d_state[grid], h.data(), sizeof(StateDesc) * b->nprob, cudaMemcpyHostToDevice),
+             "state descs copy"))
+      return HERMITE_ERR_CUDA;
+  }
+  *out = static_cast<const StateDesc *>(b->d_state[grid]);
+  *max_elems = mx;
+  return HERMITE_OK;
+}
+
 int sync_half(hermite_batch *b) {
   const int64_t h0 = b->probs[0]->half;
   for (auto *c : b->probs)
@@ -517,7 +591,10 @@ void hermite_batch_destroy(hermite_batch *b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   free_items(b);
-  for (int k = 0; k < 2; ++k) cudaFree(b->d_desc[k]);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(b->d_desc[k]);
+    cudaFree(b->d_state[k]);
+  }
   cudaFree(b->d_counters);
   for (auto *c : b->probs) hermite_destroy(c);
   delete b;
@@ -536,6 +613,42 @@ int hermite_batch_set_stream(hermite_batch *b, void *stream) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
+  return HERMITE_OK;
+}
+
+int hermite_batch_get_states_device(hermite_batch *b, int grid, double *u, double *v) {
+  if (!b) return HERMITE_ERR_ARG;
+  if ((grid != 0 && grid != 1) || !u) {
+    b->err = "bad grid or NULL u";
+    return HERMITE_ERR_ARG;
+  }
+  const StateDesc *d = nullptr;
+  int64_t mx = 0;
+  if (int rc = state_descs(b, grid, &d, &mx)) return rc;
+  const int64_t blocks = std::min<int64_t>(std::max<int64_t>((mx + 255) / 256, 1), 64);
+  batch_get_states_kernel<<<dim3((unsigned)blocks, (unsigned)b->nprob), 256, 0, b->stream>>>(d, u, v);
+  return bok(b, cudaGetLastError(), "batch_get_states_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+int hermite_batch_set_states_device(hermite_batch *b, const double *u, const double *v) {
+  if (!b) return HERMITE_ERR_ARG;
+  if (!u) {
+    b->err = "NULL u";
+    return HERMITE_ERR_ARG;
+  }
+  for (auto *c : b->probs)
+    if (c->variant == HERMITE_CONSERVATIVE) {
+      b->err = "hermite_batch_set_states_device is for the dissipative methods";
+      return HERMITE_ERR_STATE;
+    }
+  const StateDesc *d = nullptr;
+  int64_t mx = 0;
+  if (int rc = state_descs(b, HERMITE_PRIMAL, &d, &mx)) return rc;
+  const int64_t blocks = std::min<int64_t>(std::max<int64_t>((mx + 255) / 256, 1), 64);
+  batch_set_states_kernel<<<dim3((unsigned)blocks, (unsigned)b->nprob), 256, 0, b->stream>>>(d, u, v);
+  if (!bok(b, cudaGetLastError(), "batch_set_states_kernel")) return HERMITE_ERR_CUDA;
+  b->half = 0;
+  set_half(b);
   return HERMITE_OK;
 }
 

@@ -409,35 +409,48 @@ __global__ void state_to_f32_kernel(const double *__restrict__ u, const double *
   }
 }
 
+// Network input: FP32 arithmetic with reciprocals staged once per block (the
+// result is rounded to BF16); FP64 division is slow on this part.
 __global__ void pack_state_kernel(const double *__restrict__ u, const double *__restrict__ v, int64_t n, int Nu,
                                   int Nv, double vscale, const double *__restrict__ shift,
                                   const double *__restrict__ scale, int C, bf16 *__restrict__ x) {
+  __shared__ float sh_shift[64], sh_inv[64];
+  if ((int)threadIdx.x < Nu + Nv) {
+    sh_shift[threadIdx.x] = (float)shift[threadIdx.x];
+    sh_inv[threadIdx.x] = (float)(1.0 / scale[threadIdx.x]);
+  }
+  __syncthreads();
+  const float vs = (float)vscale;
   const int64_t total = n * C;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t node = i / C;
     const int c = (int)(i % C);
     float val = 0.f;
     if (c < Nu + Nv) {
-      const double s = c < Nu ? u[node * Nu + c] : vscale * v[node * Nv + (c - Nu)];
-      val = (float)((s - shift[c]) / scale[c]);
+      const float sv = c < Nu ? (float)u[node * Nu + c] : __fmul_rn((float)v[node * Nv + (c - Nu)], vs);
+      val = __fmul_rn(__fsub_rn(sv, sh_shift[c]), sh_inv[c]);
     }
     x[i] = __float2bfloat16_rn(val);
   }
 }
 
+// Residual update: the change dscale * y in FP32, added to the FP64 state.
 __global__ void unpack_state_kernel(const double *u, const double *v, const float *__restrict__ y, int64_t n, int Nu,
-                                    int Nv, double vscale, const double *__restrict__ dscale, int C, double *u_out,
+                                    int Nv, double inv_vscale, const double *__restrict__ dscale, int C, double *u_out,
                                     double *v_out) {
+  __shared__ float sh_ds[64];
+  if ((int)threadIdx.x < Nu + Nv) sh_ds[threadIdx.x] = (float)dscale[threadIdx.x];
+  __syncthreads();
   const int C0 = Nu + Nv;
   const int64_t total = n * C0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t node = i / C0;
     const int c = (int)(i % C0);
-    const double d = dscale[c] * (double)y[node * C + c];
+    const double d = (double)__fmul_rn(sh_ds[c], y[node * C + c]);
     if (c < Nu)
       u_out[node * Nu + c] = u[node * Nu + c] + d;
     else
-      v_out[node * Nv + (c - Nu)] = v[node * Nv + (c - Nu)] + d / vscale;
+      v_out[node * Nv + (c - Nu)] = fma(d, inv_vscale, v[node * Nv + (c - Nu)]);
   }
 }
 
@@ -446,6 +459,13 @@ __global__ void make_pairs_kernel(const float *__restrict__ levels, const int64_
                                   const double *__restrict__ shift, const double *__restrict__ scale,
                                   const double *__restrict__ dscale, int C, bf16 *__restrict__ x,
                                   float *__restrict__ t) {
+  __shared__ float sh_shift[64], sh_inv[64], sh_dinv[64];
+  if ((int)threadIdx.x < C0) {
+    sh_shift[threadIdx.x] = (float)shift[threadIdx.x];
+    sh_inv[threadIdx.x] = (float)(1.0 / scale[threadIdx.x]);
+    sh_dinv[threadIdx.x] = (float)(1.0 / dscale[threadIdx.x]);
+  }
+  __syncthreads();
   const int s = blockIdx.y;
   const float *a = levels + src[s];
   const float *b = levels + dst[s];
@@ -458,8 +478,8 @@ __global__ void make_pairs_kernel(const float *__restrict__ levels, const int64_
     float xv = 0.f, tv = 0.f;
     if (c < C0) {
       const float av = a[node * C0 + c], bv = b[node * C0 + c];
-      xv = (float)(((double)av - shift[c]) / scale[c]);
-      tv = (float)(((double)bv - (double)av) / dscale[c]);
+      xv = __fmul_rn(__fsub_rn(av, sh_shift[c]), sh_inv[c]);
+      tv = __fmul_rn(__fsub_rn(bv, av), sh_dinv[c]);
     }
     xs[i] = __float2bfloat16_rn(xv);
     ts[i] = tv;
@@ -514,6 +534,47 @@ __global__ void sqdiff_kernel(const double *__restrict__ au, const double *__res
     atomicAdd(out, td);
     atomicAdd(out + 1, tb);
   }
+}
+
+// per-sample distances: blockIdx.y = sample, states [nsamp][n][Nu] and [nsamp][n][Nv]
+__global__ void sqdiff_batch_kernel(const double *__restrict__ au, const double *__restrict__ av,
+                                    const double *__restrict__ bu, const double *__restrict__ bv, int64_t n, int Nu,
+                                    int Nv, double vscale, double *out) {
+  __shared__ double sh[32];
+  const int s = blockIdx.y;
+  const int64_t nu = n * Nu, nv = n * Nv, total = nu + nv;
+  au += s * nu;
+  bu += s * nu;
+  if (av) av += s * nv;
+  if (bv) bv += s * nv;
+  double sd = 0.0, sb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    double x, y;
+    if (i < nu) {
+      x = au[i];
+      y = bu[i];
+    } else {
+      x = vscale * av[i - nu];
+      y = vscale * bv[i - nu];
+    }
+    sd += (x - y) * (x - y);
+    sb += y * y;
+  }
+  const double td = block_sum(sd, sh);
+  const double tb = block_sum(sb, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(out + 2 * s, td);
+    atomicAdd(out + 2 * s + 1, tb);
+  }
+}
+
+__global__ void copy_blocks_kernel(const double *__restrict__ src, const int64_t *__restrict__ sidx,
+                                   double *__restrict__ dst, const int64_t *__restrict__ didx, int64_t block) {
+  const int i = blockIdx.y;
+  const double *a = src + (sidx ? sidx[i] : i) * block;
+  double *b = dst + (didx ? didx[i] : i) * block;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < block; e += (int64_t)gridDim.x * blockDim.x)
+    b[e] = a[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -683,7 +744,7 @@ int hnn_state_to_f32(const double *u, const double *v, int64_t n, int Nu, int Nv
 
 int hnn_pack_state(const double *u, const double *v, int64_t n, int Nu, int Nv, double vscale, const double *shift,
                    const double *scale, int C, uint16_t *x, void *stream) {
-  if (n < 0 || Nu < 1 || Nv < 0 || C < Nu + Nv) return HERMITE_ERR_ARG;
+  if (n < 0 || Nu < 1 || Nv < 0 || C < Nu + Nv || Nu + Nv > 64) return HERMITE_ERR_ARG;
   if (n == 0) return HERMITE_OK;
   if (!u || (Nv > 0 && !v) || !shift || !scale || !x) return HERMITE_ERR_ARG;
   pack_state_kernel<<<elementwise_grid(n * C), 256, 0, as_stream(stream)>>>(u, v, n, Nu, Nv, vscale, shift, scale, C,
@@ -693,18 +754,18 @@ int hnn_pack_state(const double *u, const double *v, int64_t n, int Nu, int Nv, 
 
 int hnn_unpack_state(const double *u, const double *v, const float *y, int64_t n, int Nu, int Nv, double vscale,
                      const double *dscale, int C, double *u_out, double *v_out, void *stream) {
-  if (n < 0 || Nu < 1 || Nv < 0 || C < Nu + Nv) return HERMITE_ERR_ARG;
+  if (n < 0 || Nu < 1 || Nv < 0 || C < Nu + Nv || Nu + Nv > 64 || (Nv > 0 && vscale == 0.0)) return HERMITE_ERR_ARG;
   if (n == 0) return HERMITE_OK;
   if (!u || !y || !dscale || !u_out || (Nv > 0 && (!v || !v_out))) return HERMITE_ERR_ARG;
-  unpack_state_kernel<<<elementwise_grid(n * (Nu + Nv)), 256, 0, as_stream(stream)>>>(u, v, y, n, Nu, Nv, vscale,
-                                                                                      dscale, C, u_out, v_out);
+  unpack_state_kernel<<<elementwise_grid(n * (Nu + Nv)), 256, 0, as_stream(stream)>>>(
+      u, v, y, n, Nu, Nv, Nv > 0 ? 1.0 / vscale : 0.0, dscale, C, u_out, v_out);
   return launched();
 }
 
 int hnn_make_pairs(const float *levels, const int64_t *src, const int64_t *dst, int nsamp, int64_t n, int C0,
                    const double *shift, const double *scale, const double *dscale, int C, uint16_t *x, float *t,
                    void *stream) {
-  if (nsamp < 0 || nsamp > 65535 || n < 0 || C0 < 1 || C < C0) return HERMITE_ERR_ARG;
+  if (nsamp < 0 || nsamp > 65535 || n < 0 || C0 < 1 || C0 > 64 || C < C0) return HERMITE_ERR_ARG;
   if (nsamp == 0 || n == 0) return HERMITE_OK;
   if (!levels || !src || !dst || !shift || !scale || !dscale || !x || !t) return HERMITE_ERR_ARG;
   int gx = elementwise_grid(n * C) / (nsamp < 8 ? 1 : 8);
@@ -729,6 +790,28 @@ int hnn_sqdiff(const double *a_u, const double *a_v, const double *b_u, const do
   if (!a_u || !b_u || !out || (Nv > 0 && (!a_v || !b_v))) return HERMITE_ERR_ARG;
   sqdiff_kernel<<<elementwise_grid(n * (Nu + Nv)), 256, 0, as_stream(stream)>>>(a_u, a_v, b_u, b_v, n, Nu, Nv,
                                                                                 vscale, out);
+  return launched();
+}
+
+int hnn_sqdiff_batch(const double *a_u, const double *a_v, const double *b_u, const double *b_v, int nsamp, int64_t n,
+                     int Nu, int Nv, double vscale, double *out, void *stream) {
+  if (nsamp < 0 || nsamp > 65535 || n < 0 || Nu < 1 || Nv < 0) return HERMITE_ERR_ARG;
+  if (nsamp == 0 || n == 0) return HERMITE_OK;
+  if (!a_u || !b_u || !out || (Nv > 0 && (!a_v || !b_v))) return HERMITE_ERR_ARG;
+  int gx = elementwise_grid(n * (Nu + Nv)) / 8;
+  if (gx < 1) gx = 1;
+  sqdiff_batch_kernel<<<dim3(gx, nsamp), 256, 0, as_stream(stream)>>>(a_u, a_v, b_u, b_v, n, Nu, Nv, vscale, out);
+  return launched();
+}
+
+int hnn_copy_blocks(const double *src, const int64_t *sidx, double *dst, const int64_t *didx, int nblk, int64_t block,
+                    void *stream) {
+  if (nblk < 0 || nblk > 65535 || block < 0) return HERMITE_ERR_ARG;
+  if (nblk == 0 || block == 0) return HERMITE_OK;
+  if (!src || !dst) return HERMITE_ERR_ARG;
+  int gx = elementwise_grid(block) / 8;
+  if (gx < 1) gx = 1;
+  copy_blocks_kernel<<<dim3(gx, nblk), 256, 0, as_stream(stream)>>>(src, sidx, dst, didx, block);
   return launched();
 }
 

@@ -238,40 +238,52 @@ class SuperStepper:
         c, w, a = inputs.superstep_pulses(int(traj))
         return inputs.gaussian_data_2d(self.m, self.N, self.h, PERIODIC, PRIMAL, c, w, a)
 
+    def _batch(self, B, precision=FP64):
+        import torch
+
+        b = HermiteBatch([self.problem] * B, precision=precision)
+        b.set_stream(torch.cuda.current_stream())
+        return b
+
+    def load_initial(self, batch, trajs, U, V, pool=None):
+        """Initial data of the given trajectories into the batch (one upload,
+        one batched set; slots beyond len(trajs) repeat the first)."""
+        import torch
+
+        B = len(batch.problems)
+        ids = [trajs[p] if p < len(trajs) else trajs[0] for p in range(B)]
+        ics = list(pool.map(self.initial_u, ids)) if pool is not None else [self.initial_u(t) for t in ids]
+        host = torch.from_numpy(np.stack(ics)).pin_memory()
+        U.copy_(host, non_blocking=True)
+        V.zero_()
+        batch.set_states_device(U, V)
+
     def generate(self, trajs, nlev=5, chunk=256, precision=FP64, threads=4, log=None):
         """Trajectories (list of seeds) -> FP32 metric-space levels
-        [len(trajs), nlev, N*N, C0], level k at time k K dt."""
+        [nlev, len(trajs), N*N, C0]: level k of trajectory t at time k K dt."""
         import torch
 
         trajs = list(trajs)
         nt = len(trajs)
-        levels = torch.empty((nt, nlev, self.n, self.C0), dtype=torch.float32, device="cuda")
+        levels = torch.empty((nlev, nt, self.n, self.C0), dtype=torch.float32, device="cuda")
         chunk = min(chunk, nt)
-        batch = HermiteBatch([self.problem] * chunk, precision=precision)
-        batch.set_stream(torch.cuda.current_stream())
-        U = torch.empty((chunk, self.n, self.Nu), dtype=torch.float64, device="cuda")
-        V = torch.empty((chunk, self.n, self.Nv), dtype=torch.float64, device="cuda")
+        batch = self._batch(chunk, precision)
+        U, V = self._alloc_states(chunk)
         L, s = lib(), _stream()
-        zero_v = np.zeros((self.n, self.Nv))
         t0 = time.time()
         with ThreadPoolExecutor(threads) as pool:
-            nxt = pool.map(self.initial_u, trajs[0:chunk])
             for c0 in range(0, nt, chunk):
-                ics = list(nxt)
-                if c0 + chunk < nt:
-                    nxt = pool.map(self.initial_u, trajs[c0 + chunk:c0 + 2 * chunk])
-                for p in range(chunk):
-                    batch.problem(p).set_state(ics[p] if p < len(ics) else ics[0], zero_v)
+                ids = trajs[c0:c0 + chunk]
+                self.load_initial(batch, ids, U, V, pool)
                 for k in range(nlev):
                     if k:
                         batch.step(self.K)
-                    for p in range(len(ics)):
-                        batch.problem(p).get_grid_device(PRIMAL, U[p], V[p])
-                        _check(L.hnn_state_to_f32(_p(U[p]), _p(V[p]), self.n, self.Nu, self.Nv, self.vscale,
-                                                  _p(levels[c0 + p, k]), self.C0, s), "state to f32")
+                    self.gather(batch, U, V)
+                    _check(L.hnn_state_to_f32(_p(U), _p(V), len(ids) * self.n, self.Nu, self.Nv, self.vscale,
+                                              _p(levels[k, c0]), self.C0, s), "state to f32")
                 if log:
                     torch.cuda.synchronize()
-                    log(f"generated {c0 + len(ics)}/{nt} trajectories ({time.time() - t0:.1f} s)")
+                    log(f"generated {c0 + len(ids)}/{nt} trajectories ({time.time() - t0:.1f} s)")
         torch.cuda.synchronize()
         batch.close()
         return levels
@@ -284,16 +296,14 @@ class SuperStepper:
         import torch
 
         L, s = lib(), _stream()
-        nt = min(ntraj, levels.shape[0])
+        nlev = levels.shape[0]
+        nt = min(ntraj, levels.shape[1])
         mom = torch.zeros(2 * self.C0, dtype=torch.float64, device="cuda")
         dmom = torch.zeros(2 * self.C0, dtype=torch.float64, device="cuda")
-        nlev = levels.shape[1]
-        for t in range(nt):
-            for k in range(nlev):
-                _check(L.hnn_moments(_p(levels[t, k]), None, self.n, self.C0, _p(mom), s), "moments")
-                if k + 1 < nlev:
-                    _check(L.hnn_moments(_p(levels[t, k + 1]), _p(levels[t, k]), self.n, self.C0, _p(dmom), s),
-                           "moments")
+        for k in range(nlev):
+            _check(L.hnn_moments(_p(levels[k]), None, nt * self.n, self.C0, _p(mom), s), "moments")
+            if k + 1 < nlev:
+                _check(L.hnn_moments(_p(levels[k + 1]), _p(levels[k]), nt * self.n, self.C0, _p(dmom), s), "moments")
         m = mom.cpu().numpy()
         dm = dmom.cpu().numpy()
         cnt = nt * nlev * self.n
@@ -322,13 +332,13 @@ class SuperStepper:
         import torch
 
         L, s = lib(), _stream()
-        nt, nlev = levels.shape[0], levels.shape[1]
+        nlev, nt = levels.shape[0], levels.shape[1]
         rng = np.random.default_rng(seed)
         stride = self.n * self.C0
         tr = rng.integers(0, nt, size=(iters, batch))
         kk = rng.integers(0, nlev - 1, size=(iters, batch))
-        src_all = torch.as_tensor((tr * nlev + kk) * stride, dtype=torch.int64).cuda()
-        dst_all = src_all + stride
+        src_all = torch.as_tensor((kk * nt + tr) * stride, dtype=torch.int64).cuda()
+        dst_all = src_all + nt * stride
         x = torch.empty((batch, self.N, WIDTH, CPAD), dtype=torch.bfloat16, device="cuda")
         tgt = torch.empty((batch, self.N, WIDTH, CPAD), dtype=torch.float32, device="cuda")
         loss = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -361,40 +371,38 @@ class SuperStepper:
         return torch.empty((B, self.n, self.Nu), **f64), torch.empty((B, self.n, self.Nv), **f64)
 
     def gather(self, batch, U, V):
-        for p in range(len(batch.problems)):
-            batch.problem(p).get_grid_device(PRIMAL, U[p], V[p])
+        """Primal states of every problem of the batch into U [B][n][Nu], V [B][n][Nv]."""
+        batch.get_states_device(PRIMAL, U, V)
 
     def scatter(self, batch, U, V):
-        for p in range(len(batch.problems)):
-            batch.problem(p).set_state_device(U[p], V[p])
+        batch.set_states_device(U, V)
 
-    def predict(self, U, V, outU, outV, B=None):
-        """outU/outV = network K-step prediction from states U/V (FP64, device)."""
+    def predict(self, U, V, outU, outV):
+        """outU/outV = network K-step prediction from the states U/V (FP64,
+        device, [B][n][.]); one packing launch, the network, one unpacking launch."""
         import torch
 
         L, s = lib(), _stream()
-        B = U.shape[0] if B is None else B
-        if not hasattr(self, "_x") or self._x.shape[0] != B:
+        B = U.shape[0]
+        if getattr(self, "_x", None) is None or self._x.shape[0] != B:
             self._x = torch.empty((B, self.N, WIDTH, CPAD), dtype=torch.bfloat16, device="cuda")
-        for p in range(B):
-            _check(L.hnn_pack_state(_p(U[p]), _p(V[p]), self.n, self.Nu, self.Nv, self.vscale, _p(self.shift),
-                                    _p(self.scale), CPAD, _p(self._x[p]), s), "pack")
+        _check(L.hnn_pack_state(_p(U), _p(V), B * self.n, self.Nu, self.Nv, self.vscale, _p(self.shift),
+                                _p(self.scale), CPAD, _p(self._x), s), "pack")
         y = self.net.forward(self._x, B, self.N)
-        for p in range(B):
-            _check(L.hnn_unpack_state(_p(U[p]), _p(V[p]), _p(y[p]), self.n, self.Nu, self.Nv, self.vscale,
-                                      _p(self.dscale), CPAD, _p(outU[p]), _p(outV[p]), s), "unpack")
+        _check(L.hnn_unpack_state(_p(U), _p(V), _p(y), B * self.n, self.Nu, self.Nv, self.vscale, _p(self.dscale),
+                                  CPAD, _p(outU), _p(outV), s), "unpack")
+
+    def _sqdiff(self, AU, AV, BU, BV):
+        import torch
+
+        out = torch.zeros((AU.shape[0], 2), dtype=torch.float64, device="cuda")
+        _check(lib().hnn_sqdiff_batch(_p(AU), _p(AV), _p(BU), _p(BV), AU.shape[0], self.n, self.Nu, self.Nv,
+                                      self.vscale, _p(out), _stream()), "sqdiff")
+        return out
 
     def rel_errors(self, AU, AV, BU, BV):
         """Per-sample metric-space |A - B| / |B| (FP64 device reductions)."""
-        import torch
-
-        L, s = lib(), _stream()
-        B = AU.shape[0]
-        out = torch.zeros((B, 2), dtype=torch.float64, device="cuda")
-        for p in range(B):
-            _check(L.hnn_sqdiff(_p(AU[p]), _p(AV[p]), _p(BU[p]), _p(BV[p]), self.n, self.Nu, self.Nv, self.vscale,
-                                _p(out[p]), s), "sqdiff")
-        o = out.cpu().numpy()
+        o = self._sqdiff(AU, AV, BU, BV).cpu().numpy()
         return np.sqrt(o[:, 0] / np.maximum(o[:, 1], 1e-300))
 
     def residuals(self, batch, X, A, work):
@@ -407,23 +415,18 @@ class SuperStepper:
         self.scatter(batch, *A)
         batch.step(1)
         self.gather(batch, HXu, HXv)  # now H(N(x))
-        return self.rel_errors(HXu, HXv, NHu, NHv) * (self.rel_norm(NHu, NHv) / self.rel_norm(*A))
-
-    def rel_norm(self, U, V):
-        import torch
-
-        L, s = lib(), _stream()
-        out = torch.zeros((U.shape[0], 2), dtype=torch.float64, device="cuda")
-        for p in range(U.shape[0]):
-            _check(L.hnn_sqdiff(_p(U[p]), _p(V[p]), _p(U[p]), _p(V[p]), self.n, self.Nu, self.Nv, self.vscale,
-                                _p(out[p]), s), "sqdiff")
-        return np.sqrt(out[:, 1].cpu().numpy())
+        d = self._sqdiff(HXu, HXv, NHu, NHv)
+        na = self._sqdiff(A[0], A[1], A[0], A[1])
+        o, a = d.cpu().numpy(), na.cpu().numpy()
+        return np.sqrt(o[:, 0] / np.maximum(a[:, 1], 1e-300))
 
     def advance(self, batch, bar=1e-3, check=True, fallback=True):
         """Advance every problem of batch (all at the same time level) by
         K dt: the network's prediction where the calibrated residual estimate
         is within bar, else K plain Hermite steps.  Returns (accepted mask,
         estimated errors).  The contexts' clocks restart at 0."""
+        import torch
+
         B = len(batch.problems)
         X = self._alloc_states(B)
         A = self._alloc_states(B)
@@ -438,56 +441,53 @@ class SuperStepper:
         r = self.residuals(batch, X, A, work)
         est = self.kappa * r
         acc = est <= bar
-        final_u, final_v = A[0], A[1]
         rej = np.flatnonzero(~acc)
         if len(rej) and fallback:
+            L, s = lib(), _stream()
             fb = self.fallback_batch(len(rej), batch.precision)
-            for i, p in enumerate(rej):
-                fb.problem(i).set_state_device(X[0][p], X[1][p])
+            idx = torch.as_tensor(rej, dtype=torch.int64).cuda()
+            Fu, Fv = work[0][:len(rej)], work[1][:len(rej)]
+            bu, bv = self.n * self.Nu, self.n * self.Nv
+            _check(L.hnn_copy_blocks(_p(X[0]), _p(idx), _p(Fu), None, len(rej), bu, s), "copy")
+            _check(L.hnn_copy_blocks(_p(X[1]), _p(idx), _p(Fv), None, len(rej), bv, s), "copy")
+            fb.set_states_device(Fu, Fv)
             fb.step(self.K)
-            for i, p in enumerate(rej):
-                fb.problem(i).get_grid_device(PRIMAL, final_u[p], final_v[p])
-        self.scatter(batch, final_u, final_v)
+            fb.get_states_device(PRIMAL, Fu, Fv)
+            _check(L.hnn_copy_blocks(_p(Fu), None, _p(A[0]), _p(idx), len(rej), bu, s), "copy")
+            _check(L.hnn_copy_blocks(_p(Fv), None, _p(A[1]), _p(idx), len(rej), bv, s), "copy")
+        self.scatter(batch, *A)
         return acc, est
 
     def fallback_batch(self, n, precision=FP64):
         """A batch of n problems for the rejected predictions, in the
         arithmetic of the caller's batch (kept for the next call)."""
-        import torch
-
         if self._fb is None or len(self._fb.problems) != n or self._fb.precision != precision:
             if self._fb is not None:
                 self._fb.close()
-            self._fb = HermiteBatch([self.problem] * n, precision=precision)
-            self._fb.set_stream(torch.cuda.current_stream())
+            self._fb = self._batch(n, precision)
         return self._fb
 
     def evaluate(self, trajs, chunk=256):
         """True K-step error and residual of the network on fresh initial
         data: returns (true rel. errors, residuals) per trajectory."""
-        import torch
-
         trajs = list(trajs)
         errs, ress = [], []
         B = min(chunk, len(trajs))
-        batch = HermiteBatch([self.problem] * B)
-        batch.set_stream(torch.cuda.current_stream())
+        batch = self._batch(B)
         X, A, T = self._alloc_states(B), self._alloc_states(B), self._alloc_states(B)
         work = self._alloc_states(B) + self._alloc_states(B)
-        zero_v = np.zeros((self.n, self.Nv))
-        for c0 in range(0, len(trajs), B):
-            ids = trajs[c0:c0 + B]
-            for p in range(B):
-                batch.problem(p).set_state(self.initial_u(ids[p] if p < len(ids) else ids[0]), zero_v)
-            self.gather(batch, *X)
-            self.predict(X[0], X[1], A[0], A[1])
-            batch.step(self.K)
-            self.gather(batch, *T)
-            e = self.rel_errors(A[0], A[1], T[0], T[1])
-            self.scatter(batch, *X)
-            r = self.residuals(batch, X, A, work)
-            errs.append(e[:len(ids)])
-            ress.append(r[:len(ids)])
+        with ThreadPoolExecutor(4) as pool:
+            for c0 in range(0, len(trajs), B):
+                ids = trajs[c0:c0 + B]
+                self.load_initial(batch, ids, X[0], X[1], pool)
+                self.predict(X[0], X[1], A[0], A[1])
+                batch.step(self.K)
+                self.gather(batch, *T)
+                e = self.rel_errors(A[0], A[1], T[0], T[1])
+                self.scatter(batch, *X)
+                r = self.residuals(batch, X, A, work)
+                errs.append(e[:len(ids)])
+                ress.append(r[:len(ids)])
         batch.close()
         return np.concatenate(errs), np.concatenate(ress)
 

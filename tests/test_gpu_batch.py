@@ -120,3 +120,47 @@ def test_batch_rejects_mixed_dimensions_and_unequal_progress(hb):
         batch.step(1)
     assert e.value.code == -6
     batch.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_state_transfer_matches_per_problem_calls(hb, precision):
+    """hermite_batch_get/set_states_device move every problem's level in one
+    launch, back to back, exactly like the per-problem calls."""
+    import torch
+
+    probs = [p for p in _mixed(2, 21, 9) if p[6] != 1]
+    batch = hb.HermiteBatch(probs, precision=precision)
+    batch.set_stream(torch.cuda.Stream())
+    rng = np.random.default_rng(4)
+    us, vs = [], []
+    for g in batch.problems:
+        n0 = g.nodes(0)
+        us.append(rng.standard_normal((n0, g.Nu)))
+        vs.append(rng.standard_normal((n0, g.Nv)))
+    U = torch.as_tensor(np.concatenate([u.ravel() for u in us])).cuda()
+    V = torch.as_tensor(np.concatenate([v.ravel() for v in vs])).cuda()
+    batch.set_states_device(U, V)
+    batch.step(2)
+    U2, V2 = torch.empty_like(U), torch.empty_like(V)
+    batch.get_states_device(0, U2, V2)
+    torch.cuda.synchronize()
+    ou, ov = 0, 0
+    for p, (prob, u, v) in enumerate(zip(probs, us, vs)):
+        g = batch.problem(p)
+        gu, gv = g.get_state()
+        assert np.array_equal(U2[ou:ou + gu.size].cpu().numpy().reshape(gu.shape), gu)
+        assert np.array_equal(V2[ov:ov + gv.size].cpu().numpy().reshape(gv.shape), gv)
+        single = hb.Hermite(*prob, precision=precision)
+        single.set_state(u, v)
+        single.step(2)
+        assert rel_l2(gu, single.get_state()[0]) <= 1e-13
+        ou += gu.size
+        ov += gv.size
+    cons = [p for p in _mixed(2, 21, 9) if p[6] == 1][:1]
+    if cons:
+        cb = hb.HermiteBatch(cons)
+        with pytest.raises(hb.HermiteError) as e:
+            cb.set_states_device(U, V)
+        assert e.value.code == -6
+        cb.close()
+    batch.close()

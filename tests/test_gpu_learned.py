@@ -37,7 +37,7 @@ def test_generated_levels_match_single_solver_runs(st, levels):
             u, v = g.get_state()
             s = np.concatenate([u, st.vscale * v], 1).astype(np.float32)
             # the batch kernels may round differently from a single context (1e-13)
-            assert rel_l2(lev[t, k].astype(np.float64), s.astype(np.float64)) <= 1e-7, (t, k)
+            assert rel_l2(lev[k, t].astype(np.float64), s.astype(np.float64)) <= 1e-7, (t, k)
         g.close()
 
 

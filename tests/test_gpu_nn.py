@@ -268,9 +268,12 @@ def test_state_conversions(hb):
     x = torch.empty((n, C), dtype=torch.bfloat16, device="cuda")
     assert L.hnn_pack_state(ud.data_ptr(), vd.data_ptr(), n, Nu, Nv, vs, torch.as_tensor(shift).cuda().data_ptr(),
                             torch.as_tensor(scale).cuda().data_ptr(), C, x.data_ptr(), _stream()) == 0
-    xr = ((s_ref - shift) / scale).astype(np.float32)
+    f = np.float32
+    sf = np.concatenate([u.astype(f), v.astype(f) * f(vs)], 1)
+    xr = (sf - shift.astype(f)) * (1.0 / scale).astype(f)  # the kernel's FP32 arithmetic
     got = _host(x)
     assert np.array_equal(got[:, :25], torch.as_tensor(xr).to(torch.bfloat16).float().numpy())
+    assert np.allclose(got[:, :25], (s_ref - shift) / scale, rtol=2.0 ** -8, atol=1e-6)
     assert np.all(got[:, 25:] == 0)
     y = rng.standard_normal((n, C)).astype(np.float32)
     ds = np.abs(rng.standard_normal(25)) + 0.1
@@ -279,8 +282,10 @@ def test_state_conversions(hb):
     assert L.hnn_unpack_state(ud.data_ptr(), vd.data_ptr(), _f32(y).data_ptr(), n, Nu, Nv, vs,
                               torch.as_tensor(ds).cuda().data_ptr(), C, uo.data_ptr(), vo.data_ptr(), _stream()) == 0
     torch.cuda.synchronize()
-    assert np.allclose(uo.cpu().numpy(), u + ds[:16] * y[:, :16], rtol=1e-15, atol=1e-15)
-    assert np.allclose(vo.cpu().numpy(), v + ds[16:25] * y[:, 16:25] / vs, rtol=1e-14, atol=1e-14)
+    d = (ds.astype(np.float32) * y[:, :25]).astype(np.float64)  # the FP32 change
+    assert np.allclose(uo.cpu().numpy(), u + d[:, :16], rtol=1e-15, atol=1e-15)
+    assert np.allclose(vo.cpu().numpy(), v + d[:, 16:25] / vs, rtol=1e-14, atol=1e-14)
+    assert np.allclose(uo.cpu().numpy(), u + ds[:16] * y[:, :16], rtol=1e-6, atol=1e-7)
     out2 = torch.zeros(2, dtype=torch.float64, device="cuda")
     assert L.hnn_sqdiff(uo.data_ptr(), vo.data_ptr(), ud.data_ptr(), vd.data_ptr(), n, Nu, Nv, vs, out2.data_ptr(),
                         _stream()) == 0
@@ -313,9 +318,10 @@ def test_make_pairs_and_moments(hb):
     for s, (tr, k) in enumerate(pairs):
         a = lev[tr, k].astype(np.float64)
         b = lev[tr, k + 1].astype(np.float64)
-        xr = ((a - shift) / scale).astype(np.float32)
+        f = np.float32
+        xr = (a.astype(f) - shift.astype(f)) * (1.0 / scale).astype(f)
         assert np.array_equal(xh[s, :, :C0], torch.as_tensor(xr).to(torch.bfloat16).float().numpy())
-        assert np.allclose(th[s, :, :C0], (b - a) / dscale, rtol=1e-6, atol=1e-7)
+        assert np.allclose(th[s, :, :C0], (b - a) / dscale, rtol=1e-6, atol=1e-6)
         assert np.all(xh[s, :, C0:] == 0) and np.all(th[s, :, C0:] == 0)
     mom = torch.zeros(2 * C0, dtype=torch.float64, device="cuda")
     assert L.hnn_moments(levd[0, 1].data_ptr(), levd[0, 0].data_ptr(), n, C0, mom.data_ptr(), _stream()) == 0
