@@ -74,6 +74,26 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, ws):
+    """The slowest rank's timing (every rank calls this; replicas run the same
+    work, so the job's time is the maximum).  NCCL reduces a device tensor,
+    gloo a host one."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ws, ms_max):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / (ms_max / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -217,11 +237,8 @@ def measure(hb, torch, dev, u0, v0, precision, args, ws, want_clocks):
             half_events.append(evs)
         stop.record(stream)
         torch.cuda.synchronize()
-    ms = start.elapsed_time(stop)
+    ms = max_over_ranks(start.elapsed_time(stop), ws)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     halfs = [a.elapsed_time(b) for evs in half_events for a, b in zip(evs[:-1], evs[1:])]
     half_ms = sum(halfs) / len(halfs)
@@ -254,8 +271,8 @@ def run_ours(args):
     del a, b
 
     dof_per_step = 2 * FULL_STEPS_PER_STEP * DOF_PER_HALF
-    value = ws * dof_per_step * args.steps / (split["ms"] / 1e3)
-    value64 = ws * dof_per_step * args.steps / (fp64["ms"] / 1e3)
+    value = job_throughput(dof_per_step * args.steps, ws, split["ms"])
+    value64 = job_throughput(dof_per_step * args.steps, ws, fp64["ms"])
 
     # end to end through the public API with host buffers: H2D of the state,
     # the step, and D2H of the state and the energy
@@ -275,8 +292,8 @@ def run_ours(args):
         one_step()
         g.get_state(ou.numpy(), ov.numpy())
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value = ws * dof_per_step / e2e_s
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+    e2e_value = job_throughput(dof_per_step, ws, 1e3 * e2e_s)
     state_bytes = NODES * (NU + NV) * 8
     g.close()
 
