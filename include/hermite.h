@@ -115,6 +115,12 @@ int hermite_set_state_device(hermite_ctx *ctx, const double *u, const double *v)
  * [nodes_primal][Nu] and u_dual at t = dt/2 [nodes_dual][Nu]. */
 int hermite_set_state2(hermite_ctx *ctx, const double *u_primal, const double *u_dual);
 
+/* Testing hook (process-wide, no counterpart in the paper): the n-th device
+ * allocation the library makes after this call fails as if the device were
+ * out of memory (the call that made it returns HERMITE_ERR_ALLOC and frees
+ * what it had allocated); n = 0 turns the hook off.  HERMITE_ERR_ARG if n < 0. */
+int hermite_debug_fail_alloc(int n);
+
 /* Advance n >= 0 full steps (2n half-steps), device work only, enqueued on
  * the context's stream (asynchronous with respect to the host). */
 int hermite_step(hermite_ctx *ctx, int64_t nsteps);

@@ -60,6 +60,12 @@ int hnn_set_conv_engine(int engine);
  * call (its output is then incomplete), else HERMITE_OK. */
 int hnn_conv_status(void);
 
+/* Self-test of the failure path: one block waits on an mbarrier that nothing
+ * arrives at; its bounded wait (2^22 polls, well under a few seconds) gives up
+ * and records the error that the next hnn_conv_status returns
+ * (HERMITE_ERR_TIMEOUT).  The context stays usable. */
+int hnn_wait_selftest(void *stream);
+
 /* Self-test of the tensor-core path on one CTA: D[128][N] = A[128][64] B[N][64]^T,
  * A and B BF16 row-major, D FP32 row-major, N = 32 or 64; *status (device int,
  * caller-initialised to 0) is set to 1 if the MMA completion wait ran out. */

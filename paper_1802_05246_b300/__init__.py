@@ -39,6 +39,7 @@ EXPORTS = [
     "hnn_conv3x3_fwd", "hnn_flip_weights", "hnn_conv3x3_wgrad", "hnn_bias_grad", "hnn_mse", "hnn_adam",
     "hnn_state_to_f32", "hnn_pack_state", "hnn_unpack_state", "hnn_make_pairs", "hnn_moments", "hnn_sqdiff",
     "hnn_set_conv_engine", "hnn_conv_status", "hnn_tc_gemm_selftest", "hnn_sqdiff_batch", "hnn_copy_blocks",
+    "hnn_wait_selftest", "hermite_debug_fail_alloc",
 ]
 
 
@@ -112,6 +113,8 @@ def lib():
         "hnn_tc_gemm_selftest": (c_int, [vp, vp, vp, c_int, vp, vp]),
         "hnn_sqdiff_batch": (c_int, [vp, vp, vp, vp, c_int, i64, c_int, c_int, c_dbl, vp, vp]),
         "hnn_copy_blocks": (c_int, [vp, vp, vp, vp, c_int, i64, vp]),
+        "hnn_wait_selftest": (c_int, [vp]),
+        "hermite_debug_fail_alloc": (c_int, [c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -1,4 +1,5 @@
 // C ABI of the Hermite library (declarations and contracts: include/hermite.h).
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -14,6 +15,24 @@ bool cuda_ok(hermite_ctx *ctx, cudaError_t e, const char *what) {
   if (e == cudaSuccess) return true;
   if (ctx) ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
   return false;
+}
+
+namespace {
+std::atomic<int> g_fail_alloc{0};  // > 0: the g_fail_alloc-th next allocation fails
+}
+
+cudaError_t device_alloc(void **p, size_t bytes) {
+  int n = g_fail_alloc.load();
+  while (n > 0) {
+    if (g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+      if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
 }
 
 }  // namespace hermite
@@ -261,7 +280,7 @@ int create_context(int d, int m, int64_t N, double c, double h, double dt, int v
   const int64_t maxld = std::max(ctx->ld[0], ctx->ld[1]);
   auto alloc = [&](void **p, size_t bytes, const char *what) {
     if (rc) return;
-    if (!cuda_ok(ctx, cudaMalloc(p, bytes ? bytes : 8), what)) rc = HERMITE_ERR_ALLOC;
+    if (!cuda_ok(ctx, device_alloc(p, bytes ? bytes : 8), what)) rc = HERMITE_ERR_ALLOC;
   };
   for (int g = 0; g < 2; ++g) alloc((void **)&ctx->grid[g], sizeof(double) * ctx->ncoef * ctx->ld[g], "grid");
   alloc((void **)&ctx->M, sizeof(double) * ctx->nco * ctx->nci, "operator");
@@ -350,6 +369,12 @@ int hermite_set_state2(hermite_ctx *ctx, const double *u_primal, const double *u
   if (rc == HERMITE_OK) rc = sync_split_from_fp64(ctx);
   if (rc == HERMITE_OK) ctx->half = 0;
   return rc;
+}
+
+int hermite_debug_fail_alloc(int n) {
+  if (n < 0) return HERMITE_ERR_ARG;
+  g_fail_alloc.store(n);
+  return HERMITE_OK;
 }
 
 int hermite_step(hermite_ctx *ctx, int64_t nsteps) {

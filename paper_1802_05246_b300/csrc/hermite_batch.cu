@@ -361,7 +361,7 @@ int build_items(hermite_batch *b) {
       std::vector<BatchItem> items(h.size());
       for (size_t i = 0; i < h.size(); ++i) items[i] = h[i].it;
       hermite_batch::Group gr{key, nullptr, (int)items.size()};
-      if (!bok(b, cudaMalloc(&gr.d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)), "cudaMalloc items") ||
+      if (!bok(b, device_alloc(&gr.d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)), "cudaMalloc items") ||
           !bok(b, cudaMemcpy(gr.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice),
                "items copy"))
         return HERMITE_ERR_CUDA;
@@ -372,7 +372,7 @@ int build_items(hermite_batch *b) {
   if (need > b->ncounters) {
     cudaFree(b->d_counters);
     b->d_counters = nullptr;
-    if (!bok(b, cudaMalloc(&b->d_counters, sizeof(unsigned) * need), "cudaMalloc counters")) return HERMITE_ERR_ALLOC;
+    if (!bok(b, device_alloc(&b->d_counters, sizeof(unsigned) * need), "cudaMalloc counters")) return HERMITE_ERR_ALLOC;
     b->ncounters = need;
   }
   return HERMITE_OK;
@@ -402,7 +402,7 @@ int build_descs(hermite_batch *b) {
       ds.nco = c->nco;
       ds.sub = c->variant == HERMITE_CONSERVATIVE ? 1 : 0;
     }
-    if (!bok(b, cudaMalloc(&b->d_desc[k], sizeof(BatchDesc) * b->nprob), "cudaMalloc descs") ||
+    if (!bok(b, device_alloc(&b->d_desc[k], sizeof(BatchDesc) * b->nprob), "cudaMalloc descs") ||
         !bok(b, cudaMemcpy(b->d_desc[k], h.data(), sizeof(BatchDesc) * b->nprob, cudaMemcpyHostToDevice),
              "descs copy"))
       return HERMITE_ERR_CUDA;
@@ -515,10 +515,14 @@ int state_descs(hermite_batch *b, int grid, const StateDesc **out, int64_t *max_
     mx = std::max<int64_t>(mx, D.nodes * (D.Nu + D.Nv));
   }
   if (!b->d_state[grid]) {
-    if (!bok(b, cudaMalloc(&b->d_state[grid], sizeof(StateDesc) * b->nprob), "cudaMalloc state descs") ||
-        !bok(b, cudaMemcpy(b->d_state[grid], h.data(), sizeof(StateDesc) * b->nprob, cudaMemcpyHostToDevice),
-             "state descs copy"))
+    if (!bok(b, device_alloc(&b->d_state[grid], sizeof(StateDesc) * b->nprob), "cudaMalloc state descs"))
+      return HERMITE_ERR_ALLOC;
+    if (!bok(b, cudaMemcpy(b->d_state[grid], h.data(), sizeof(StateDesc) * b->nprob, cudaMemcpyHostToDevice),
+             "state descs copy")) {
+      cudaFree(b->d_state[grid]);
+      b->d_state[grid] = nullptr;
       return HERMITE_ERR_CUDA;
+    }
   }
   *out = static_cast<const StateDesc *>(b->d_state[grid]);
   *max_elems = mx;

@@ -111,4 +111,12 @@ int create_context(int d, int m, int64_t N, double c, double h, double dt, int v
                    bool with_energy, hermite_ctx **out);
 bool cuda_ok(hermite_ctx *ctx, cudaError_t e, const char *what);
 
+// Every device allocation of the library goes through here: cudaMalloc, unless
+// hermite_debug_fail_alloc asked this call to fail (tests of the clean-up paths).
+cudaError_t device_alloc(void **p, size_t bytes);
+template <class T>
+inline cudaError_t device_alloc(T **p, size_t bytes) {
+  return device_alloc(reinterpret_cast<void **>(p), bytes);
+}
+
 }  // namespace hermite

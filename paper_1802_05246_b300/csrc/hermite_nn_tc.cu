@@ -480,6 +480,18 @@ __global__ void __launch_bounds__(320, 1)
   if (tid == 0 && read_flag(&s_err)) atomicExch(&g_tc_status, 1);
 }
 
+// Failure-path self-test: one block waits on an mbarrier that nothing arrives
+// at; the bounded wait gives up and records the error.
+__global__ void wait_selftest_kernel() {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicExch(&g_tc_status, 1);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -578,6 +590,11 @@ int hnn_conv_status(void) {
     return HERMITE_ERR_TIMEOUT;
   }
   return HERMITE_OK;
+}
+
+int hnn_wait_selftest(void *stream) {
+  wait_selftest_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>();
+  return cudaGetLastError() == cudaSuccess ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
 int hnn_tc_gemm_selftest(const uint16_t *A, const uint16_t *B, float *D, int N, int *status, void *stream) {

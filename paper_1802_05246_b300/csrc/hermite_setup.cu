@@ -454,11 +454,11 @@ struct Basis {
 
 int make_basis(hermite_ctx *ctx, Basis &bs) {
   const int m = ctx->m;
-  if (!cuda_ok(ctx, cudaMalloc(&bs.Hm, sizeof(double) * (2 * m + 2) * (m + 1)), "cudaMalloc basis"))
+  if (!cuda_ok(ctx, device_alloc(&bs.Hm, sizeof(double) * (2 * m + 2) * (m + 1)), "cudaMalloc basis"))
     return HERMITE_ERR_ALLOC;
   basis_kernel<<<1, 1, 0, ctx->stream>>>(m, bs.Hm);
   if (m >= 1) {
-    if (!cuda_ok(ctx, cudaMalloc(&bs.Hm1, sizeof(double) * (2 * m) * m), "cudaMalloc basis"))
+    if (!cuda_ok(ctx, device_alloc(&bs.Hm1, sizeof(double) * (2 * m) * m), "cudaMalloc basis"))
       return HERMITE_ERR_ALLOC;
     basis_kernel<<<1, 1, 0, ctx->stream>>>(m - 1, bs.Hm1);
   }
@@ -477,10 +477,10 @@ int build_cholesky_factor(hermite_ctx *ctx, int f, int nclass, int nq) {
   int *rank = nullptr;
   int rc = HERMITE_OK;
   const size_t n2 = (size_t)nclass * nq * nq;
-  if (!cuda_ok(ctx, cudaMalloc(&work, sizeof(double) * n2), "cudaMalloc chol work") ||
-      !cuda_ok(ctx, cudaMalloc(&rank, sizeof(int) * nclass), "cudaMalloc rank") ||
-      !cuda_ok(ctx, cudaMalloc(&ctx->L[f], sizeof(double) * n2), "cudaMalloc L") ||
-      !cuda_ok(ctx, cudaMalloc(&ctx->lperm[f], sizeof(int16_t) * nclass * nq), "cudaMalloc perm")) {
+  if (!cuda_ok(ctx, device_alloc(&work, sizeof(double) * n2), "cudaMalloc chol work") ||
+      !cuda_ok(ctx, device_alloc(&rank, sizeof(int) * nclass), "cudaMalloc rank") ||
+      !cuda_ok(ctx, device_alloc(&ctx->L[f], sizeof(double) * n2), "cudaMalloc L") ||
+      !cuda_ok(ctx, device_alloc(&ctx->lperm[f], sizeof(int16_t) * nclass * nq), "cudaMalloc perm")) {
     rc = HERMITE_ERR_ALLOC;
   } else {
     pivoted_cholesky_kernel<<<1, 32, 0, ctx->stream>>>(ctx->Q[f], nclass, nq, work, ctx->L[f], ctx->lperm[f], rank);
@@ -512,9 +512,9 @@ int build_lowrank_factor(hermite_ctx *ctx, int f, const double *F, int nclass, i
   const size_t nF = (size_t)npoly * P.B;
   double *R = nullptr, *RF = nullptr, *work = nullptr;
   int rc = HERMITE_OK;
-  if (!cuda_ok(ctx, cudaMalloc(&R, sizeof(double) * P.E * P.E), "cudaMalloc R") ||
-      !cuda_ok(ctx, cudaMalloc(&RF, sizeof(double) * nF), "cudaMalloc RF") ||
-      !cuda_ok(ctx, cudaMalloc(&work, sizeof(double) * nF), "cudaMalloc work")) {
+  if (!cuda_ok(ctx, device_alloc(&R, sizeof(double) * P.E * P.E), "cudaMalloc R") ||
+      !cuda_ok(ctx, device_alloc(&RF, sizeof(double) * nF), "cudaMalloc RF") ||
+      !cuda_ok(ctx, device_alloc(&work, sizeof(double) * nF), "cudaMalloc work")) {
     rc = HERMITE_ERR_ALLOC;
   } else {
     gram_cholesky_kernel<<<1, 1, 0, ctx->stream>>>(P.E, R);
@@ -548,8 +548,8 @@ int build_lowrank_factor(hermite_ctx *ctx, int f, const double *F, int nclass, i
                   h[(((size_t)c * nq + b) * ncomp + rows[c][r].first) * P.B + rows[c][r].second];
         std::vector<int16_t> ident((size_t)nclass * nq);
         for (size_t i = 0; i < ident.size(); ++i) ident[i] = (int16_t)(i % nq);
-        if (!cuda_ok(ctx, cudaMalloc(&ctx->L[f], sizeof(double) * Lh.size()), "cudaMalloc L") ||
-            !cuda_ok(ctx, cudaMalloc(&ctx->lperm[f], sizeof(int16_t) * ident.size()), "cudaMalloc perm")) {
+        if (!cuda_ok(ctx, device_alloc(&ctx->L[f], sizeof(double) * Lh.size()), "cudaMalloc L") ||
+            !cuda_ok(ctx, device_alloc(&ctx->lperm[f], sizeof(int16_t) * ident.size()), "cudaMalloc perm")) {
           rc = HERMITE_ERR_ALLOC;
         } else if (!cuda_ok(ctx, cudaMemcpy(ctx->L[f], Lh.data(), sizeof(double) * Lh.size(), cudaMemcpyHostToDevice),
                             "L copy") ||
@@ -602,7 +602,7 @@ int build_operator(hermite_ctx *ctx, bool startup, double *out, int rows, int co
     p.tau = 0.5 * ctx->lam;
     p.vscale = ctx->h / ctx->c;
     p.out = out;
-    if (!cuda_ok(ctx, cudaMalloc(&work, sizeof(double) * (size_t)cols * 8 * p.P.B), "cudaMalloc work")) {
+    if (!cuda_ok(ctx, device_alloc(&work, sizeof(double) * (size_t)cols * 8 * p.P.B), "cudaMalloc work")) {
       rc = HERMITE_ERR_ALLOC;
     } else {
       p.work = work;
@@ -635,10 +635,10 @@ int build_energy_forms(hermite_ctx *ctx) {
     const int ncomp = (kind == kConsSemi) ? 1 : (kind == kConsGrad ? ctx->d : ctx->d + 1);
     double *F = nullptr, *HF = nullptr, *work = nullptr;
     const size_t nF = (size_t)nclass * nq * ncomp * P.B;
-    if (!cuda_ok(ctx, cudaMalloc(&F, sizeof(double) * nF), "cudaMalloc F") ||
-        !cuda_ok(ctx, cudaMalloc(&HF, sizeof(double) * nF), "cudaMalloc HF") ||
-        !cuda_ok(ctx, cudaMalloc(&work, sizeof(double) * (size_t)nclass * nq * 4 * P.B), "cudaMalloc work") ||
-        !cuda_ok(ctx, cudaMalloc(&ctx->Q[f], sizeof(double) * (size_t)nclass * nq * nq), "cudaMalloc Q")) {
+    if (!cuda_ok(ctx, device_alloc(&F, sizeof(double) * nF), "cudaMalloc F") ||
+        !cuda_ok(ctx, device_alloc(&HF, sizeof(double) * nF), "cudaMalloc HF") ||
+        !cuda_ok(ctx, device_alloc(&work, sizeof(double) * (size_t)nclass * nq * 4 * P.B), "cudaMalloc work") ||
+        !cuda_ok(ctx, device_alloc(&ctx->Q[f], sizeof(double) * (size_t)nclass * nq * nq), "cudaMalloc Q")) {
       rc = HERMITE_ERR_ALLOC;
     } else {
       FormParams p;
@@ -699,7 +699,7 @@ int build_parity_tables(hermite_ctx *ctx) {
       par.push_back((int8_t)bits);
     }
   }
-  if (!cuda_ok(ctx, cudaMalloc(&ctx->par_in, par.size() + 1), "cudaMalloc parity")) return HERMITE_ERR_ALLOC;
+  if (!cuda_ok(ctx, device_alloc(&ctx->par_in, par.size() + 1), "cudaMalloc parity")) return HERMITE_ERR_ALLOC;
   if (!cuda_ok(ctx, cudaMemcpy(ctx->par_in, par.data(), par.size(), cudaMemcpyHostToDevice), "parity copy"))
     return HERMITE_ERR_CUDA;
   ctx->par_out = ctx->par_in;

@@ -477,9 +477,9 @@ int build_split_operator(hermite_ctx *ctx) {
     outrow[(size_t)c * ctx->nomax + npc[c]] = (int16_t)r;
     npc[c]++;
   }
-  if (!cuda_ok(ctx, cudaMalloc(&ctx->outrow, sizeof(int16_t) * outrow.size()), "cudaMalloc outrow") ||
-      !cuda_ok(ctx, cudaMalloc(&ctx->npc, nclass), "cudaMalloc npc") ||
-      !cuda_ok(ctx, cudaMalloc(&ctx->Mc, sizeof(float2) * (size_t)nclass * ctx->nci * ctx->nomax), "cudaMalloc Mc"))
+  if (!cuda_ok(ctx, device_alloc(&ctx->outrow, sizeof(int16_t) * outrow.size()), "cudaMalloc outrow") ||
+      !cuda_ok(ctx, device_alloc(&ctx->npc, nclass), "cudaMalloc npc") ||
+      !cuda_ok(ctx, device_alloc(&ctx->Mc, sizeof(float2) * (size_t)nclass * ctx->nci * ctx->nomax), "cudaMalloc Mc"))
     return HERMITE_ERR_ALLOC;
   if (!cuda_ok(ctx, cudaMemcpy(ctx->outrow, outrow.data(), sizeof(int16_t) * outrow.size(), cudaMemcpyHostToDevice),
                "outrow copy") ||
@@ -495,7 +495,7 @@ int build_split_operator(hermite_ctx *ctx) {
 int build_split_forms(hermite_ctx *ctx) {
   for (int f = 0; f < kNumForms; ++f) {
     const int64_t n = (int64_t)(1 << ctx->d) * ctx->lrows[f] * ctx->nq[f];
-    if (!cuda_ok(ctx, cudaMalloc(&ctx->Lf[f], sizeof(float2) * std::max<int64_t>(n, 1)), "cudaMalloc Lf"))
+    if (!cuda_ok(ctx, device_alloc(&ctx->Lf[f], sizeof(float2) * std::max<int64_t>(n, 1)), "cudaMalloc Lf"))
       return HERMITE_ERR_ALLOC;
     split_factor_kernel<<<64, 256, 0, ctx->stream>>>(ctx->L[f], n, ctx->Lf[f]);
   }
