@@ -145,69 +145,6 @@ __global__ void __launch_bounds__(kEThreads) energy_kernel(Geometry g, const dou
   if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
-// Low-rank form Q_c = L_c^T L_c: E_cell = sum_r (L_r . y_c(A)) (L_r . y_c(B)).
-template <int D>
-__global__ void __launch_bounds__(kEThreads) energy_lowrank_kernel(Geometry g, const double *__restrict__ L,
-                                                                   int rmax, int nq,
-                                                                   const int8_t *__restrict__ par,
-                                                                   const double *__restrict__ A,
-                                                                   const double *__restrict__ B, double *partials) {
-  extern __shared__ double sm[];
-  const int c = blockIdx.y;
-  const bool quad = (A == B);
-  double *Ls = sm;                                   // [rmax][nq]
-  double *ya = Ls + (size_t)rmax * nq;               // [nq][kEThreads]
-  double *ybv = quad ? ya : ya + (size_t)nq * kEThreads;
-  int8_t *pin = reinterpret_cast<int8_t *>(ya + (size_t)(quad ? 1 : 2) * nq * kEThreads);
-  __shared__ double red[kEThreads];
-  const double *Lc = L + (size_t)c * rmax * nq;
-  for (int i = threadIdx.x; i < rmax * nq; i += kEThreads) Ls[i] = Lc[i];
-  for (int i = threadIdx.x; i < nq; i += kEThreads) pin[i] = par[i];
-  __syncthreads();
-  double total = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * kEThreads;
-  for (int64_t t = (int64_t)blockIdx.x * kEThreads + threadIdx.x; t < g.nodes_dst; t += stride) {
-    int64_t idx[1 << D];
-    int gm[1 << D];
-    double w;
-    cell_corners_e<D>(g, t, idx, gm, &w);
-    for (int b = 0; b < nq; ++b) {
-      ya[b * kEThreads + threadIdx.x] = class_value<D>(A + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
-      if (!quad)
-        ybv[b * kEThreads + threadIdx.x] =
-            class_value<D>(B + (size_t)b * g.ld_src, idx, gm, g.bc, pin[b], c ^ pin[b]);
-    }
-    double cell = 0.0;
-    for (int r = 0; r < rmax; ++r) {
-      const double *lrow = Ls + (size_t)r * nq;
-      double sa0 = 0.0, sa1 = 0.0, sb0 = 0.0, sb1 = 0.0;
-      int k = 0;
-      for (; k + 1 < nq; k += 2) {
-        sa0 = fma(lrow[k], ya[k * kEThreads + threadIdx.x], sa0);
-        sa1 = fma(lrow[k + 1], ya[(k + 1) * kEThreads + threadIdx.x], sa1);
-        if (!quad) {
-          sb0 = fma(lrow[k], ybv[k * kEThreads + threadIdx.x], sb0);
-          sb1 = fma(lrow[k + 1], ybv[(k + 1) * kEThreads + threadIdx.x], sb1);
-        }
-      }
-      for (; k < nq; ++k) {
-        sa0 = fma(lrow[k], ya[k * kEThreads + threadIdx.x], sa0);
-        if (!quad) sb0 = fma(lrow[k], ybv[k * kEThreads + threadIdx.x], sb0);
-      }
-      const double la = sa0 + sa1;
-      cell = fma(la, quad ? la : (sb0 + sb1), cell);
-    }
-    total = fma(w, cell, total);
-  }
-  red[threadIdx.x] = total;
-  __syncthreads();
-  for (int off = kEThreads / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
-}
-
 // Factored form Q_c = L_c^T L_c (L_c upper triangular in a permuted column
 // order, or a short dense low-rank factor): a block takes a tile of 64 cells
 // and one class, stages their class vectors y_c (columns permuted) in shared
