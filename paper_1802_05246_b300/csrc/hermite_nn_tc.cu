@@ -119,21 +119,6 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 // three 32-column loads under one wait (the epilogue's D_0, D_2 and D_1)
 __device__ __forceinline__ void tc_ld32x3(uint32_t t0, uint32_t t1, uint32_t t2, float (&a)[32], float (&b)[32],
                                           float (&c)[32]) {
@@ -151,15 +136,6 @@ __device__ __forceinline__ void tc_ld32x3(uint32_t t0, uint32_t t1, uint32_t t2,
     a[i] = __uint_as_float(r[i]);
     b[i] = __uint_as_float(r[32 + i]);
     c[i] = __uint_as_float(r[64 + i]);
-  }
-}
-template <int N>
-__device__ __forceinline__ void tc_ld(uint32_t taddr, float (&v)[N]) {
-  if constexpr (N == 32) {
-    tc_ld32(taddr, v);
-  } else {
-    static_assert(N == 16, "16 or 32 columns");
-    tc_ld16(taddr, v);
   }
 }
 
@@ -420,9 +396,9 @@ __global__ void __launch_bounds__(320, 1)
       if constexpr (C::CH == 32) {
         tc_ld32x3(tbase, tbase + 2 * COUT, tbase + COUT, d0, d2, acc);
       } else {
-        tc_ld<C::CH>(tbase, d0);
-        tc_ld<C::CH>(tbase + 2 * COUT, d2);
-        tc_ld<C::CH>(tbase + COUT, acc);
+        tc_ld16(tbase, d0);
+        tc_ld16(tbase + 2 * COUT, d2);
+        tc_ld16(tbase + COUT, acc);
       }
       tc_fence_before();
       mbar_arrive(tempty + a);
