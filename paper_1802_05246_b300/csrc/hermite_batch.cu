@@ -418,8 +418,13 @@ int launch_group(hermite_batch *b, int k, const hermite_batch::Group &gr, unsign
     switch (gr.tmpl) {
       case 2: batch_split_kernel<D, 2><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       case 4: batch_split_kernel<D, 4><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 6: batch_split_kernel<D, 6><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       case 8: batch_split_kernel<D, 8><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 10: batch_split_kernel<D, 10><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 12: batch_split_kernel<D, 12><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 14: batch_split_kernel<D, 14><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       case 16: batch_split_kernel<D, 16><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
+      case 24: batch_split_kernel<D, 24><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       case 32: batch_split_kernel<D, 32><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
       default: return HERMITE_ERR_ARG;
     }

@@ -244,8 +244,13 @@ int launch_split_d(hermite_ctx *ctx, const Geometry &g, const float2 *src, float
   switch (ctx->nomax) {
     case 2: return launch_split_dn<D, 2>(ctx, g, src, dst, sub);
     case 4: return launch_split_dn<D, 4>(ctx, g, src, dst, sub);
+    case 6: return launch_split_dn<D, 6>(ctx, g, src, dst, sub);
     case 8: return launch_split_dn<D, 8>(ctx, g, src, dst, sub);
+    case 10: return launch_split_dn<D, 10>(ctx, g, src, dst, sub);
+    case 12: return launch_split_dn<D, 12>(ctx, g, src, dst, sub);
+    case 14: return launch_split_dn<D, 14>(ctx, g, src, dst, sub);
     case 16: return launch_split_dn<D, 16>(ctx, g, src, dst, sub);
+    case 24: return launch_split_dn<D, 24>(ctx, g, src, dst, sub);
     case 32: return launch_split_dn<D, 32>(ctx, g, src, dst, sub);
   }
   return HERMITE_ERR_ARG;
@@ -468,7 +473,8 @@ int build_split_operator(hermite_ctx *ctx) {
   int nomax = 0;
   for (int c = 0; c < nclass; ++c) nomax = std::max(nomax, counts[c]);
   // slots per class warp: the smallest even count that holds the largest class
-  ctx->nomax = nomax <= 2 ? 2 : (nomax <= 4 ? 4 : (nomax <= 8 ? 8 : (nomax <= 16 ? 16 : 32)));
+  // (up to 16; then 24 or 32)
+  ctx->nomax = nomax <= 16 ? std::max(2, (nomax + 1) / 2 * 2) : (nomax <= 24 ? 24 : 32);
   if (nomax > 32) return HERMITE_ERR_UNSUPPORTED;
   std::vector<int16_t> outrow((size_t)nclass * ctx->nomax, -1);
   std::vector<int8_t> npc(nclass, 0);
