@@ -76,12 +76,13 @@ __device__ __forceinline__ double gsign(int bc, int mask, int pb) {
 // class-c component of the corner Walsh-Hadamard transform of coefficient b
 template <int D>
 __device__ __forceinline__ double class_value(const double *__restrict__ plane, const int64_t *idx, const int *gm,
-                                              int bc, int pb, int q) {
+                                              int bc, int pb, int q, int stride = 1) {
   double acc = 0.0;
 #pragma unroll
   for (int s = 0; s < (1 << D); ++s) {
-    double v = __ldg(plane + idx[s]);
-    if (gm[s]) v *= gsign(bc, gm[s], pb);
+    double v = __ldg(plane + idx[s * stride]);
+    const int gs = gm[s * stride];
+    if (gs) v *= gsign(bc, gs, pb);
     acc += (__popc(q & s) & 1) ? -v : v;
   }
   return acc;
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(kFThreads) energy_factored_kernel(
   double *YA = Ls + (size_t)rmax * nq;                // [kFTile][ld]
   double *YB = quad ? YA : YA + (size_t)kFTile * ld;  // [kFTile][ld]
   double *cw = YA + (size_t)(quad ? 1 : 2) * kFTile * ld;  // [kFTile]
-  int64_t *cidx = reinterpret_cast<int64_t *>(cw + kFTile);  // [kFTile][NC]
-  int *cgm = reinterpret_cast<int *>(cidx + kFTile * NC);    // [kFTile][NC]
+  int64_t *cidx = reinterpret_cast<int64_t *>(cw + kFTile);  // [NC][kFTile]: lanes of a warp read consecutive words
+  int *cgm = reinterpret_cast<int *>(cidx + kFTile * NC);    // [NC][kFTile]
   int16_t *ps = reinterpret_cast<int16_t *>(cgm + kFTile * NC);  // [nq]
   int8_t *pin = reinterpret_cast<int8_t *>(ps + nq);             // [nq]
   __shared__ double red[kFThreads];
@@ -185,27 +186,31 @@ __global__ void __launch_bounds__(kFThreads) energy_factored_kernel(
     __syncthreads();
     if (threadIdx.x < kFTile) {
       const int64_t t = tile * kFTile + threadIdx.x;
+      int64_t li[NC];
+      int lg[NC];
+      double w = 0.0;
       if (t < g.nodes_dst) {
-        double w;
-        cell_corners_e<D>(g, t, cidx + threadIdx.x * NC, cgm + threadIdx.x * NC, &w);
-        cw[threadIdx.x] = w;
+        cell_corners_e<D>(g, t, li, lg, &w);
       } else {
         for (int s = 0; s < NC; ++s) {
-          cidx[threadIdx.x * NC + s] = 0;
-          cgm[threadIdx.x * NC + s] = 0;
+          li[s] = 0;
+          lg[s] = 0;
         }
-        cw[threadIdx.x] = 0.0;
       }
+      for (int s = 0; s < NC; ++s) {
+        cidx[s * kFTile + threadIdx.x] = li[s];
+        cgm[s * kFTile + threadIdx.x] = lg[s];
+      }
+      cw[threadIdx.x] = w;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < kFTile * nq; e += kFThreads) {
       // consecutive lanes take consecutive cells of one coefficient plane so
       // that their corner gathers coalesce
       const int i = e % kFTile, k = e / kFTile, b = ps[k];
-      YA[i * ld + k] = class_value<D>(A + (size_t)b * g.ld_src, cidx + i * NC, cgm + i * NC, g.bc, pin[b], c ^ pin[b]);
+      YA[i * ld + k] = class_value<D>(A + (size_t)b * g.ld_src, cidx + i, cgm + i, g.bc, pin[b], c ^ pin[b], kFTile);
       if (!quad)
-        YB[i * ld + k] =
-            class_value<D>(B + (size_t)b * g.ld_src, cidx + i * NC, cgm + i * NC, g.bc, pin[b], c ^ pin[b]);
+        YB[i * ld + k] = class_value<D>(B + (size_t)b * g.ld_src, cidx + i, cgm + i, g.bc, pin[b], c ^ pin[b], kFTile);
     }
     __syncthreads();
     double e4[4] = {0.0, 0.0, 0.0, 0.0};

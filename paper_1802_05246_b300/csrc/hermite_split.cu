@@ -295,8 +295,10 @@ __global__ void __launch_bounds__(kSFThreads) energy_factored_split_kernel(
     if (threadIdx.x < kSFTile) {
       const int64_t t = tile * kSFTile + threadIdx.x;
       double w = 0.0;
+      int64_t li[NC];
+      int lg[NC];
       if (t < g.nodes_dst) {
-        corners_split<D>(g, t, cidx + threadIdx.x * NC, cgm + threadIdx.x * NC);
+        corners_split<D>(g, t, li, lg);
         int64_t r = t;
         w = 1.0;
         for (int i = D - 1; i >= 0; --i) {
@@ -307,9 +309,14 @@ __global__ void __launch_bounds__(kSFThreads) energy_factored_split_kernel(
         }
       } else {
         for (int s = 0; s < NC; ++s) {
-          cidx[threadIdx.x * NC + s] = 0;
-          cgm[threadIdx.x * NC + s] = 0;
+          li[s] = 0;
+          lg[s] = 0;
         }
+      }
+      // corner-major ([NC][kSFTile]): the lanes of a warp read consecutive words
+      for (int s = 0; s < NC; ++s) {
+        cidx[s * kSFTile + threadIdx.x] = li[s];
+        cgm[s * kSFTile + threadIdx.x] = lg[s];
       }
       cw[threadIdx.x] = w;
     }
@@ -318,16 +325,18 @@ __global__ void __launch_bounds__(kSFThreads) energy_factored_split_kernel(
       // consecutive lanes take consecutive cells of one coefficient plane so
       // that their corner gathers coalesce
       const int i = e % kSFTile, k = e / kSFTile, b = ps[k], q = c ^ pin[b];
-      const int64_t *idx = cidx + i * NC;
-      const int *gm = cgm + i * NC;
+      const int64_t *idx = cidx + i;
+      const int *gm = cgm + i;
       float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
 #pragma unroll
       for (int s = 0; s < NC; ++s) {
-        const bool neg = ((__popc(q & s) & 1) != 0) != (gm[s] && ghost_negates(g.bc, gm[s], pin[b]));
-        float2 v = A[(size_t)b * g.ld_src + idx[s]];
+        const int gs = gm[s * kSFTile];
+        const int64_t is = idx[s * kSFTile];
+        const bool neg = ((__popc(q & s) & 1) != 0) != (gs && ghost_negates(g.bc, gs, pin[b]));
+        float2 v = A[(size_t)b * g.ld_src + is];
         ya = df_add(ya, neg ? df_neg(v) : v);
         if (!quad) {
-          v = B[(size_t)b * g.ld_src + idx[s]];
+          v = B[(size_t)b * g.ld_src + is];
           yb = df_add(yb, neg ? df_neg(v) : v);
         }
       }

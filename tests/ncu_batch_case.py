@@ -1,0 +1,27 @@
+"""Small case for an ncu capture of the ragged-batch split kernel (not a test):
+the first 128 problems of the seed-0 ragged 2-D workload (N in
+{32,64,128,256}^2, m in 2..6, mixed boundaries), dissipative, split precision,
+two full steps on a non-default stream.  Usage: python tests/ncu_batch_case.py"""
+import os
+import sys
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import paper_1802_05246_b300 as hb  # noqa: E402
+
+rng = np.random.default_rng(0)
+probs = []
+for _ in range(128):
+    Np = int(rng.choice([32, 64, 128, 256]))
+    m = int(rng.integers(2, 7))
+    bc = int(rng.integers(0, 3))
+    rng.integers(1, 5)  # pulse draws of the workload generator are not needed here
+    probs.append((2, m, Np, 1.0, 1.0 / Np, 0.9 / Np, hb.DISSIPATIVE, bc))
+b = hb.HermiteBatch(probs, precision=hb.SPLIT32)
+b.set_stream(torch.cuda.Stream())
+b.step(2)
+torch.cuda.synchronize()
+print("ok", b.dof_per_step)

@@ -1,0 +1,18 @@
+"""Small case for an ncu capture of the energy kernels (not a test): 3-D,
+m = 3, 64^3 periodic, dissipative, split precision, random data; one energy
+call (two forms).  Usage: python tests/ncu_energy_case.py"""
+import os
+import sys
+
+import torch
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import paper_1802_05246_b300 as hb  # noqa: E402
+
+N, m = 64, 3
+h = 1.0 / N
+g = hb.Hermite(3, m, N, 1.0, h, 0.9 * h, hb.DISSIPATIVE, hb.PERIODIC, precision=hb.SPLIT32)
+u = torch.randn(N ** 3, (m + 1) ** 3, dtype=torch.float64, device="cuda")
+v = torch.randn(N ** 3, m ** 3, dtype=torch.float64, device="cuda")
+g.set_state_device(u, v)
+print("ok", g.energy())
