@@ -104,7 +104,7 @@ __device__ __forceinline__ bool ghost_negates(int bc, int mask, int pb) {
 }
 
 template <int D, int NOMAX>
-__global__ void __launch_bounds__(32 << D) half_step_split_kernel(
+__global__ void __launch_bounds__(32 << D, 2) half_step_split_kernel(
     Geometry g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow, const int8_t *__restrict__ npc,
     int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src, float2 *__restrict__ dst,
     int subtract_old) {
@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(32 << D) half_step_split_kernel(
   constexpr int NT = 32 * NC;
   extern __shared__ float2 sm2[];
   float2 *Ms = sm2;                               // [NC class][nci][NOMAX]
-  float2 *Ybuf = Ms + (size_t)NC * nci * NOMAX;   // 2 x [NC beta slot][NC class][32]
-  int8_t *pin = reinterpret_cast<int8_t *>(Ybuf + 2 * NC * NC * 32);
+  float2 *Ybuf = Ms + (size_t)NC * nci * NOMAX;   // [NC beta slot][NC class][32]
+  int8_t *pin = reinterpret_cast<int8_t *>(Ybuf + NC * NC * 32);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < NC * nci * NOMAX; i += NT) Ms[i] = Mc[i];
   for (int i = threadIdx.x; i < nci; i += NT) pin[i] = par[i];
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(32 << D) half_step_split_kernel(
     if (nchunks > 1) load(NC);
     __syncthreads();
     for (int ch = 0; ch < nchunks; ++ch) {
-      const float2 *Y = Ybuf + (ch & 1) * NC * NC * 32;
+      const float2 *Y = Ybuf;
       const int b0 = ch * NC;
       const int kmax = min(NC, nci - b0);
       // every slot runs (unused slots multiply zeros) so that the NOMAX
@@ -196,10 +196,13 @@ __global__ void __launch_bounds__(32 << D) half_step_split_kernel(
       } else {
         for (int k = 0; k < kmax; ++k) consume(k);
       }
-      // the next chunk (already loaded) goes into the other buffer and the
-      // loads of the one after are issued before the barrier
+      // the next chunk (already loaded) replaces this one once every warp has
+      // consumed it, and the loads of the one after are issued before the
+      // barrier.  One buffer keeps the block at about 110 KB of shared memory
+      // (3-D, m = 3), so two blocks share an SM and cover each other's barriers.
+      __syncthreads();
       if (ch + 1 < nchunks) {
-        transform((ch + 1) * NC, Ybuf + ((ch + 1) & 1) * NC * NC * 32);
+        transform((ch + 1) * NC, Ybuf);
         if (ch + 2 < nchunks) load((ch + 2) * NC);
       }
       __syncthreads();
@@ -223,7 +226,7 @@ template <int D, int NOMAX>
 int launch_split_dn(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub) {
   constexpr int NC = 1 << D;
   auto kern = half_step_split_kernel<D, NOMAX>;
-  const size_t smem = sizeof(float2) * ((size_t)NC * ctx->nci * NOMAX + 2 * NC * NC * 32) + ctx->nci + 16;
+  const size_t smem = sizeof(float2) * ((size_t)NC * ctx->nci * NOMAX + NC * NC * 32) + ctx->nci + 16;
   static thread_local int configured_dev = -1;
   if (configured_dev != ctx->device) {
     if (!cuda_ok(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
