@@ -103,17 +103,18 @@ __device__ __forceinline__ bool ghost_negates(int bc, int mask, int pb) {
   return neg != 0;
 }
 
-template <int D, int NOMAX>
-__global__ void __launch_bounds__(32 << D, 2) half_step_split_kernel(
-    Geometry g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow, const int8_t *__restrict__ npc,
-    int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src, float2 *__restrict__ dst,
-    int subtract_old) {
+template <int D, int NOMAX, int NBUF>
+__device__ __forceinline__ void half_step_split_body(
+    const Geometry &g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow,
+    const int8_t *__restrict__ npc, int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src,
+    float2 *__restrict__ dst, int subtract_old) {
   constexpr int NC = 1 << D;
   constexpr int NT = 32 * NC;
+  constexpr int YSZ = NC * NC * 32;
   extern __shared__ float2 sm2[];
   float2 *Ms = sm2;                               // [NC class][nci][NOMAX]
-  float2 *Ybuf = Ms + (size_t)NC * nci * NOMAX;   // [NC beta slot][NC class][32]
-  int8_t *pin = reinterpret_cast<int8_t *>(Ybuf + NC * NC * 32);
+  float2 *Ybuf = Ms + (size_t)NC * nci * NOMAX;   // NBUF x [NC beta slot][NC class][32]
+  int8_t *pin = reinterpret_cast<int8_t *>(Ybuf + NBUF * YSZ);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < NC * nci * NOMAX; i += NT) Ms[i] = Mc[i];
   for (int i = threadIdx.x; i < nci; i += NT) pin[i] = par[i];
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(32 << D, 2) half_step_split_kernel(
     if (nchunks > 1) load(NC);
     __syncthreads();
     for (int ch = 0; ch < nchunks; ++ch) {
-      const float2 *Y = Ybuf;
+      const float2 *Y = Ybuf + (NBUF == 2 ? (ch & 1) * YSZ : 0);
       const int b0 = ch * NC;
       const int kmax = min(NC, nci - b0);
       // every slot runs (unused slots multiply zeros) so that the NOMAX
@@ -196,13 +197,14 @@ __global__ void __launch_bounds__(32 << D, 2) half_step_split_kernel(
       } else {
         for (int k = 0; k < kmax; ++k) consume(k);
       }
-      // the next chunk (already loaded) replaces this one once every warp has
-      // consumed it, and the loads of the one after are issued before the
-      // barrier.  One buffer keeps the block at about 110 KB of shared memory
-      // (3-D, m = 3), so two blocks share an SM and cover each other's barriers.
-      __syncthreads();
+      // the next chunk (already loaded) goes into the other buffer, or, with
+      // one buffer, replaces this one once every warp has consumed it; the
+      // loads of the chunk after are issued before the barrier.  One buffer is
+      // used where it is what lets two blocks share an SM (3-D, m = 3: 110 KB
+      // instead of 125 KB), so that they cover each other's barriers.
+      if (NBUF == 1) __syncthreads();
       if (ch + 1 < nchunks) {
-        transform((ch + 1) * NC, Ybuf);
+        transform((ch + 1) * NC, Ybuf + (NBUF == 2 ? ((ch + 1) & 1) * YSZ : 0));
         if (ch + 2 < nchunks) load((ch + 2) * NC);
       }
       __syncthreads();
@@ -222,11 +224,27 @@ __global__ void __launch_bounds__(32 << D, 2) half_step_split_kernel(
   }
 }
 
+// Two entry points: two exchange buffers with the compiler's own register
+// budget, and one buffer with a budget that keeps two blocks per SM.
 template <int D, int NOMAX>
-int launch_split_dn(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub) {
-  constexpr int NC = 1 << D;
-  auto kern = half_step_split_kernel<D, NOMAX>;
-  const size_t smem = sizeof(float2) * ((size_t)NC * ctx->nci * NOMAX + NC * NC * 32) + ctx->nci + 16;
+__global__ void __launch_bounds__(32 << D) half_step_split_kernel(
+    Geometry g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow, const int8_t *__restrict__ npc,
+    int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src, float2 *__restrict__ dst,
+    int subtract_old) {
+  half_step_split_body<D, NOMAX, 2>(g, Mc, outrow, npc, nci, par, src, dst, subtract_old);
+}
+
+template <int D, int NOMAX>
+__global__ void __launch_bounds__(32 << D, 2) half_step_split_1buf_kernel(
+    Geometry g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow, const int8_t *__restrict__ npc,
+    int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src, float2 *__restrict__ dst,
+    int subtract_old) {
+  half_step_split_body<D, NOMAX, 1>(g, Mc, outrow, npc, nci, par, src, dst, subtract_old);
+}
+
+template <int D, int NOMAX, int NBUF>
+int launch_split_dnb(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub, size_t smem) {
+  auto kern = NBUF == 2 ? half_step_split_kernel<D, NOMAX> : half_step_split_1buf_kernel<D, NOMAX>;
   static thread_local int configured_dev = -1;
   if (configured_dev != ctx->device) {
     if (!cuda_ok(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
@@ -237,9 +255,23 @@ int launch_split_dn(hermite_ctx *ctx, const Geometry &g, const float2 *src, floa
   if (g.nodes_dst == 0) return HERMITE_OK;
   const int64_t nblk = (g.nodes_dst + 31) / 32;
   const int64_t blocks = std::min<int64_t>(nblk, 148 * 16);
-  kern<<<(unsigned)blocks, 32 * NC, smem, ctx->stream>>>(g, ctx->Mc, ctx->outrow, ctx->npc, ctx->nci, ctx->par_in,
+  kern<<<(unsigned)blocks, 32 << D, smem, ctx->stream>>>(g, ctx->Mc, ctx->outrow, ctx->npc, ctx->nci, ctx->par_in,
                                                           src, dst, sub ? 1 : 0);
   return cuda_ok(ctx, cudaGetLastError(), "half_step_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+
+// Two exchange buffers, unless a single one is what lets two blocks share an
+// SM (3-D, m = 3: 110 KB instead of 125 KB); then the blocks cover each
+// other's extra barrier.
+template <int D, int NOMAX>
+int launch_split_dn(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub) {
+  constexpr int NC = 1 << D;
+  const size_t base = sizeof(float2) * (size_t)NC * ctx->nci * NOMAX + ctx->nci + 16;
+  const size_t ybytes = sizeof(float2) * NC * NC * 32;
+  constexpr size_t kTwoBlocks = 112 * 1024;
+  if (base + 2 * ybytes > kTwoBlocks && base + ybytes <= kTwoBlocks)
+    return launch_split_dnb<D, NOMAX, 1>(ctx, g, src, dst, sub, base + ybytes);
+  return launch_split_dnb<D, NOMAX, 2>(ctx, g, src, dst, sub, base + 2 * ybytes);
 }
 
 template <int D>
