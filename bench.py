@@ -253,11 +253,11 @@ def run_ours(args):
     import paper_1802_05246_b300 as hb
 
     ws, rank, local = dist_env()
+    torch.cuda.set_device(local)  # before the process group, so NCCL binds this rank's GPU
     if ws > 1:
         import torch.distributed as dist
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     u0, v0 = initial_state()
 
