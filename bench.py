@@ -318,7 +318,7 @@ def run_ours(args):
                    "step": "8 full time steps (16 half-steps) + 1 energy reduction",
                    "l2": "inputs larger than L2 (3.05 GB read+written per half-step vs 126 MB)",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "alu", "kernel": "half_step_split_kernel<3,16>", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "half_step_split_kernel<3,12,10>", "achieved": achieved,
                      "peak": FP32_NOMINAL_TOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_NOMINAL_TOPS,
                      "peak_source": "FP32 pipe nominal (148 SMs x 128 lanes x 2.032 GHz, operations/s); "

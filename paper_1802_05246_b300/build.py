@@ -26,14 +26,24 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source to an object file (in parallel, the kernel
+    instantiations make some files slow) and link the shared library."""
     if not force and not _stale():
         return LIB
+    import concurrent.futures
+    import tempfile
+
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-lineinfo", *ARCH,
-           "-I", os.path.join(HERE, "..", "include"), "-o", tmp, *sources()]
+    flags = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo", *ARCH, "-I", os.path.join(HERE, "..", "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+        flags.insert(0, "-Xptxas=-v")
+    with tempfile.TemporaryDirectory() as objdir:
+        srcs = sources()
+        objs = [os.path.join(objdir, os.path.basename(s) + ".o") for s in srcs]
+        with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+            for f in [ex.submit(subprocess.check_call, [NVCC, *flags, "-c", s, "-o", o]) for s, o in zip(srcs, objs)]:
+                f.result()
+        subprocess.check_call([NVCC, "-shared", *ARCH, "-o", tmp, *objs])
     os.replace(tmp, LIB)
     return LIB
 

@@ -80,6 +80,9 @@ void release(hermite_ctx *ctx) {
   cudaFree(ctx->fscratch);
   cudaFree(ctx->outrow);
   cudaFree(ctx->npc);
+  if (ctx->Mp != ctx->Mc) cudaFree(ctx->Mp);
+  if (ctx->prow != ctx->outrow) cudaFree(ctx->prow);
+  cudaFree(ctx->pcls);
 }
 
 bool is_split(const hermite_ctx *ctx) { return ctx->precision == HERMITE_SPLIT32; }

@@ -73,6 +73,13 @@ struct hermite_ctx {
   int16_t *outrow = nullptr;   // [2^d][nomax] output row of each class slot (-1 unused)
   int8_t *npc = nullptr;       // outputs per class
   int nomax = 0;
+  // slot packing of the single-problem split half-step: warp w's slots
+  // [0, psplit) hold outputs of parity class pcls[2w], slots [psplit, pslots)
+  // outputs of class pcls[2w+1]; the operator is laid out per warp
+  float2 *Mp = nullptr;        // [2^d warp][nci][pslots]
+  int16_t *prow = nullptr;     // [2^d][pslots] output row of each slot (-1 unused)
+  int8_t *pcls = nullptr;      // [2^d][2]
+  int pslots = 0, psplit = 0;
   std::string err;
 };
 

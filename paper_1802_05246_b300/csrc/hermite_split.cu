@@ -7,8 +7,10 @@
 //
 // Work split inside a block of 32 target nodes and 2^d warps: in phase A warp
 // w transforms input coefficient b0+w for the 32 nodes and writes its 2^d
-// class components to shared memory; in phase B warp w owns parity class w
-// and accumulates the outputs of that class.  Each corner value is loaded
+// class components to shared memory; in phase B warp w accumulates S output
+// slots, the first P of one parity class and the rest of a second one (the
+// classes differ in size, so packing two per warp keeps the warps' slot
+// counts, and the padding multiply-adds, small).  Each corner value is loaded
 // and transformed once per node.
 #include <algorithm>
 #include <vector>
@@ -103,22 +105,23 @@ __device__ __forceinline__ bool ghost_negates(int bc, int mask, int pb) {
   return neg != 0;
 }
 
-template <int D, int NOMAX, int NBUF>
+template <int D, int S, int P, int NBUF>
 __device__ __forceinline__ void half_step_split_body(
-    const Geometry &g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow,
-    const int8_t *__restrict__ npc, int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src,
+    const Geometry &g, const float2 *__restrict__ Mp, const int16_t *__restrict__ prow,
+    const int8_t *__restrict__ pcls, int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src,
     float2 *__restrict__ dst, int subtract_old) {
+  static_assert(S % 2 == 0 && P > 0 && P <= S, "slot layout");
   constexpr int NC = 1 << D;
   constexpr int NT = 32 * NC;
   constexpr int YSZ = NC * NC * 32;
   extern __shared__ float2 sm2[];
-  float2 *Ms = sm2;                               // [NC class][nci][NOMAX]
-  float2 *Ybuf = Ms + (size_t)NC * nci * NOMAX;   // NBUF x [NC beta slot][NC class][32]
+  float2 *Ms = sm2;                           // [NC warp][nci][S]
+  float2 *Ybuf = Ms + (size_t)NC * nci * S;   // NBUF x [NC beta slot][NC class][32]
   int8_t *pin = reinterpret_cast<int8_t *>(Ybuf + NBUF * YSZ);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < NC * nci * NOMAX; i += NT) Ms[i] = Mc[i];
+  for (int i = threadIdx.x; i < NC * nci * S; i += NT) Ms[i] = Mp[i];
   for (int i = threadIdx.x; i < nci; i += NT) pin[i] = par[i];
-  const int np = npc[w];
+  const int cA = pcls[2 * w], cB = pcls[2 * w + 1];
   __syncthreads();
   const int64_t nblk = (g.nodes_dst + 31) / 32;
   const int nchunks = (nci + NC - 1) / NC;
@@ -166,9 +169,9 @@ __device__ __forceinline__ void half_step_split_body(
 #pragma unroll
       for (int q = 0; q < NC; ++q) Y[(w * NC + q) * 32 + lane] = x[q];
     };
-    float2 acc[NOMAX];
+    float2 acc[S];
 #pragma unroll
-    for (int j = 0; j < NOMAX; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < S; ++j) acc[j] = make_float2(0.f, 0.f);
     load(0);
     transform(0, Ybuf);
     if (nchunks > 1) load(NC);
@@ -182,13 +185,15 @@ __device__ __forceinline__ void half_step_split_body(
       // 16 bytes at a time
       auto consume = [&](int k) {
         const int bb = b0 + k;
-        const float2 y = Y[(k * NC + (w ^ pin[bb])) * 32 + lane];
-        const float4 *mrow = reinterpret_cast<const float4 *>(Ms + ((size_t)w * nci + bb) * NOMAX);
+        const int pb = pin[bb];
+        const float2 ya = Y[(k * NC + (cA ^ pb)) * 32 + lane];
+        const float2 yb = P < S ? Y[(k * NC + (cB ^ pb)) * 32 + lane] : ya;
+        const float4 *mrow = reinterpret_cast<const float4 *>(Ms + ((size_t)w * nci + bb) * S);
 #pragma unroll
-        for (int j = 0; j < NOMAX / 2; ++j) {
+        for (int j = 0; j < S / 2; ++j) {
           const float4 mm = mrow[j];
-          df_fma(acc[2 * j], make_float2(mm.x, mm.y), y);
-          df_fma(acc[2 * j + 1], make_float2(mm.z, mm.w), y);
+          df_fma(acc[2 * j], make_float2(mm.x, mm.y), 2 * j < P ? ya : yb);
+          df_fma(acc[2 * j + 1], make_float2(mm.z, mm.w), 2 * j + 1 < P ? ya : yb);
         }
       };
       if (kmax == NC) {
@@ -211,9 +216,9 @@ __device__ __forceinline__ void half_step_split_body(
     }
     if (valid) {
 #pragma unroll
-      for (int j = 0; j < NOMAX; ++j) {
-        if (j < np) {
-          const int row = outrow[w * NOMAX + j];
+      for (int j = 0; j < S; ++j) {
+        const int row = prow[w * S + j];
+        if (row >= 0) {
           float2 *o = dst + (size_t)row * g.ld_dst + t;
           float2 r = df_norm(acc[j]);
           if (subtract_old) r = df_norm(df_add(r, df_neg(*o)));
@@ -226,25 +231,25 @@ __device__ __forceinline__ void half_step_split_body(
 
 // Two entry points: two exchange buffers with the compiler's own register
 // budget, and one buffer with a budget that keeps two blocks per SM.
-template <int D, int NOMAX>
+template <int D, int S, int P>
 __global__ void __launch_bounds__(32 << D) half_step_split_kernel(
-    Geometry g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow, const int8_t *__restrict__ npc,
+    Geometry g, const float2 *__restrict__ Mp, const int16_t *__restrict__ prow, const int8_t *__restrict__ pcls,
     int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src, float2 *__restrict__ dst,
     int subtract_old) {
-  half_step_split_body<D, NOMAX, 2>(g, Mc, outrow, npc, nci, par, src, dst, subtract_old);
+  half_step_split_body<D, S, P, 2>(g, Mp, prow, pcls, nci, par, src, dst, subtract_old);
 }
 
-template <int D, int NOMAX>
+template <int D, int S, int P>
 __global__ void __launch_bounds__(32 << D, 2) half_step_split_1buf_kernel(
-    Geometry g, const float2 *__restrict__ Mc, const int16_t *__restrict__ outrow, const int8_t *__restrict__ npc,
+    Geometry g, const float2 *__restrict__ Mp, const int16_t *__restrict__ prow, const int8_t *__restrict__ pcls,
     int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src, float2 *__restrict__ dst,
     int subtract_old) {
-  half_step_split_body<D, NOMAX, 1>(g, Mc, outrow, npc, nci, par, src, dst, subtract_old);
+  half_step_split_body<D, S, P, 1>(g, Mp, prow, pcls, nci, par, src, dst, subtract_old);
 }
 
-template <int D, int NOMAX, int NBUF>
+template <int D, int S, int P, int NBUF>
 int launch_split_dnb(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub, size_t smem) {
-  auto kern = NBUF == 2 ? half_step_split_kernel<D, NOMAX> : half_step_split_1buf_kernel<D, NOMAX>;
+  auto kern = NBUF == 2 ? half_step_split_kernel<D, S, P> : half_step_split_1buf_kernel<D, S, P>;
   static thread_local int configured_dev = -1;
   if (configured_dev != ctx->device) {
     if (!cuda_ok(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
@@ -255,39 +260,64 @@ int launch_split_dnb(hermite_ctx *ctx, const Geometry &g, const float2 *src, flo
   if (g.nodes_dst == 0) return HERMITE_OK;
   const int64_t nblk = (g.nodes_dst + 31) / 32;
   const int64_t blocks = std::min<int64_t>(nblk, 148 * 16);
-  kern<<<(unsigned)blocks, 32 << D, smem, ctx->stream>>>(g, ctx->Mc, ctx->outrow, ctx->npc, ctx->nci, ctx->par_in,
+  kern<<<(unsigned)blocks, 32 << D, smem, ctx->stream>>>(g, ctx->Mp, ctx->prow, ctx->pcls, ctx->nci, ctx->par_in,
                                                           src, dst, sub ? 1 : 0);
   return cuda_ok(ctx, cudaGetLastError(), "half_step_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
 // Two exchange buffers, unless a single one is what lets two blocks share an
-// SM (3-D, m = 3: 110 KB instead of 125 KB); then the blocks cover each
-// other's extra barrier.
-template <int D, int NOMAX>
+// SM (3-D, m = 3 with one class per warp: 110 KB instead of 125 KB); then the
+// blocks cover each other's extra barrier.
+template <int D, int S, int P>
 int launch_split_dn(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub) {
   constexpr int NC = 1 << D;
-  const size_t base = sizeof(float2) * (size_t)NC * ctx->nci * NOMAX + ctx->nci + 16;
+  const size_t base = sizeof(float2) * (size_t)NC * ctx->nci * S + ctx->nci + 16;
   const size_t ybytes = sizeof(float2) * NC * NC * 32;
-  constexpr size_t kTwoBlocks = 112 * 1024;
-  if (base + 2 * ybytes > kTwoBlocks && base + ybytes <= kTwoBlocks)
-    return launch_split_dnb<D, NOMAX, 1>(ctx, g, src, dst, sub, base + ybytes);
-  return launch_split_dnb<D, NOMAX, 2>(ctx, g, src, dst, sub, base + 2 * ybytes);
+  if constexpr (D == 3) {
+    constexpr size_t kTwoBlocks = 112 * 1024;
+    if (base + 2 * ybytes > kTwoBlocks && base + ybytes <= kTwoBlocks)
+      return launch_split_dnb<D, S, P, 1>(ctx, g, src, dst, sub, base + ybytes);
+  }
+  return launch_split_dnb<D, S, P, 2>(ctx, g, src, dst, sub, base + 2 * ybytes);
 }
+
+// Slot layouts (S slots per warp, the first P of one class) with a compiled
+// kernel: one class per warp (P = S), and for d > 1 two classes per warp.
+constexpr int kOneClassLayouts[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
+constexpr int kTwoClassLayouts[][2] = {{4, 2},   {6, 4},   {8, 6},   {10, 8},  {12, 10}, {14, 12},
+                                       {16, 14}, {20, 16}, {24, 20}, {28, 24}, {32, 28}};
 
 template <int D>
 int launch_split_d(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub) {
-  switch (ctx->nomax) {
-    case 2: return launch_split_dn<D, 2>(ctx, g, src, dst, sub);
-    case 4: return launch_split_dn<D, 4>(ctx, g, src, dst, sub);
-    case 6: return launch_split_dn<D, 6>(ctx, g, src, dst, sub);
-    case 8: return launch_split_dn<D, 8>(ctx, g, src, dst, sub);
-    case 10: return launch_split_dn<D, 10>(ctx, g, src, dst, sub);
-    case 12: return launch_split_dn<D, 12>(ctx, g, src, dst, sub);
-    case 14: return launch_split_dn<D, 14>(ctx, g, src, dst, sub);
-    case 16: return launch_split_dn<D, 16>(ctx, g, src, dst, sub);
-    case 24: return launch_split_dn<D, 24>(ctx, g, src, dst, sub);
-    case 32: return launch_split_dn<D, 32>(ctx, g, src, dst, sub);
+  const int S = ctx->pslots, P = ctx->psplit;
+#define HERMITE_SPLIT_LAYOUT(S_, P_) \
+  if (S == S_ && P == P_) return launch_split_dn<D, S_, P_>(ctx, g, src, dst, sub);
+  HERMITE_SPLIT_LAYOUT(2, 2)
+  HERMITE_SPLIT_LAYOUT(4, 4)
+  HERMITE_SPLIT_LAYOUT(6, 6)
+  HERMITE_SPLIT_LAYOUT(8, 8)
+  HERMITE_SPLIT_LAYOUT(10, 10)
+  HERMITE_SPLIT_LAYOUT(12, 12)
+  HERMITE_SPLIT_LAYOUT(14, 14)
+  HERMITE_SPLIT_LAYOUT(16, 16)
+  HERMITE_SPLIT_LAYOUT(20, 20)
+  HERMITE_SPLIT_LAYOUT(24, 24)
+  HERMITE_SPLIT_LAYOUT(28, 28)
+  HERMITE_SPLIT_LAYOUT(32, 32)
+  if constexpr (D > 1) {
+    HERMITE_SPLIT_LAYOUT(4, 2)
+    HERMITE_SPLIT_LAYOUT(6, 4)
+    HERMITE_SPLIT_LAYOUT(8, 6)
+    HERMITE_SPLIT_LAYOUT(10, 8)
+    HERMITE_SPLIT_LAYOUT(12, 10)
+    HERMITE_SPLIT_LAYOUT(14, 12)
+    HERMITE_SPLIT_LAYOUT(16, 14)
+    HERMITE_SPLIT_LAYOUT(20, 16)
+    HERMITE_SPLIT_LAYOUT(24, 20)
+    HERMITE_SPLIT_LAYOUT(28, 24)
+    HERMITE_SPLIT_LAYOUT(32, 28)
   }
+#undef HERMITE_SPLIT_LAYOUT
   return HERMITE_ERR_ARG;
 }
 
@@ -504,6 +534,48 @@ __global__ void from_split_kernel(const float2 *__restrict__ a, int64_t ld, int 
   }
 }
 
+// Can warps of S slots, the first P for one parity class and the other S - P
+// for one more, hold counts[c] outputs of every class?  Each class takes some
+// number of P-slot bins and then enough (S - P)-slot bins for the rest; a
+// dynamic programme over the classes finds an assignment using at most one
+// bin of each kind per warp.  On success bins[w] and bins[nclass + w] are the
+// classes of warp w's two bins (-1: unused).
+bool pack_two_classes(const std::vector<int> &counts, int S, int P, std::vector<int> *bins) {
+  const int nclass = (int)counts.size(), s = S - P;
+  // reach[c][big][small]: classes < c placed with that many bins used; choice
+  // records the big-bin count of class c - 1
+  std::vector<std::vector<std::vector<int>>> choice(
+      nclass + 1, std::vector<std::vector<int>>(nclass + 1, std::vector<int>(nclass + 1, -1)));
+  choice[0][0][0] = 0;
+  for (int c = 0; c < nclass; ++c)
+    for (int bu = 0; bu <= nclass; ++bu)
+      for (int su = 0; su <= nclass; ++su) {
+        if (choice[c][bu][su] < 0) continue;
+        for (int b = 0; bu + b <= nclass; ++b) {
+          const int rest = std::max(0, counts[c] - b * P);
+          const int k = rest == 0 ? 0 : (s > 0 ? (rest + s - 1) / s : nclass + 1);
+          if (su + k <= nclass && choice[c + 1][bu + b][su + k] < 0) choice[c + 1][bu + b][su + k] = b;
+        }
+      }
+  for (int bu = 0; bu <= nclass; ++bu)
+    for (int su = 0; su <= nclass; ++su) {
+      if (choice[nclass][bu][su] < 0) continue;
+      bins->assign(2 * nclass, -1);
+      int wb = 0, ws = 0, b_left = bu, s_left = su;
+      for (int c = nclass - 1; c >= 0; --c) {
+        const int b = choice[c + 1][b_left][s_left];
+        const int rest = std::max(0, counts[c] - b * P);
+        const int k = rest == 0 ? 0 : (rest + s - 1) / s;
+        for (int i = 0; i < b; ++i) (*bins)[wb++] = c;
+        for (int i = 0; i < k; ++i) (*bins)[nclass + ws++] = c;
+        b_left -= b;
+        s_left -= k;
+      }
+      return true;
+    }
+  return false;
+}
+
 }  // namespace
 
 int build_split_operator(hermite_ctx *ctx) {
@@ -529,14 +601,69 @@ int build_split_operator(hermite_ctx *ctx) {
   }
   if (!cuda_ok(ctx, device_alloc(&ctx->outrow, sizeof(int16_t) * outrow.size()), "cudaMalloc outrow") ||
       !cuda_ok(ctx, device_alloc(&ctx->npc, nclass), "cudaMalloc npc") ||
-      !cuda_ok(ctx, device_alloc(&ctx->Mc, sizeof(float2) * (size_t)nclass * ctx->nci * ctx->nomax), "cudaMalloc Mc"))
+      !cuda_ok(ctx, device_alloc(&ctx->Mc, sizeof(float2) * (size_t)nclass * ctx->nci * ctx->nomax), "cudaMalloc Mc") ||
+      !cuda_ok(ctx, device_alloc(&ctx->pcls, 2 * nclass), "cudaMalloc pcls"))
     return HERMITE_ERR_ALLOC;
   if (!cuda_ok(ctx, cudaMemcpy(ctx->outrow, outrow.data(), sizeof(int16_t) * outrow.size(), cudaMemcpyHostToDevice),
                "outrow copy") ||
       !cuda_ok(ctx, cudaMemcpy(ctx->npc, npc.data(), nclass, cudaMemcpyHostToDevice), "npc copy"))
     return HERMITE_ERR_CUDA;
   split_operator_kernel<<<64, 256, 0, ctx->stream>>>(ctx->M, ctx->nci, ctx->outrow, nclass, ctx->nomax, ctx->Mc);
-  if (!cuda_ok(ctx, cudaGetLastError(), "split_operator_kernel") ||
+  if (!cuda_ok(ctx, cudaGetLastError(), "split_operator_kernel")) return HERMITE_ERR_CUDA;
+
+  // the single-problem kernel: two classes per warp where that needs fewer
+  // slots, else the class layout above
+  std::vector<std::vector<int>> rows(nclass);
+  for (int r = 0; r < ctx->nco; ++r) rows[parh[r]].push_back(r);
+  std::vector<int> bins;
+  int S = ctx->nomax, P = ctx->nomax;
+  const int cmax = *std::max_element(counts.begin(), counts.end());
+  for (int cand = 2; cand < ctx->nomax && S == ctx->nomax; cand += 2) {
+    if (cmax <= cand && std::find(std::begin(kOneClassLayouts), std::end(kOneClassLayouts), cand) !=
+                            std::end(kOneClassLayouts)) {
+      bins.assign(2 * nclass, -1);
+      for (int w = 0; w < nclass; ++w) bins[w] = w;
+      S = P = cand;
+    } else if (nclass > 1) {
+      for (const auto &l : kTwoClassLayouts)
+        if (l[0] == cand && pack_two_classes(counts, l[0], l[1], &bins)) {
+          S = l[0];
+          P = l[1];
+          break;
+        }
+    }
+  }
+  std::vector<int8_t> cls(2 * nclass);
+  if (S == ctx->nomax) {
+    for (int w = 0; w < nclass; ++w) cls[2 * w] = cls[2 * w + 1] = (int8_t)w;
+    ctx->Mp = ctx->Mc;
+    ctx->prow = ctx->outrow;
+  } else {
+    // bins[w] / bins[nclass + w]: class of warp w's first P / last S - P slots
+    std::vector<int16_t> prow((size_t)nclass * S, -1);
+    std::vector<size_t> next(nclass, 0);
+    for (int part = 0; part < 2; ++part)
+      for (int w = 0; w < nclass; ++w) {
+        const int c = bins[part * nclass + w];
+        const int j0 = part ? P : 0, j1 = part ? S : P;
+        cls[2 * w + part] = (int8_t)(c < 0 ? (part ? cls[2 * w] : 0) : c);
+        for (int j = j0; j < j1 && c >= 0 && next[c] < rows[c].size(); ++j)
+          prow[(size_t)w * S + j] = (int16_t)rows[c][next[c]++];
+      }
+    for (int c = 0; c < nclass; ++c)
+      if (next[c] != rows[c].size()) return HERMITE_ERR_UNSUPPORTED;  // not reached: the packing covers every row
+    if (!cuda_ok(ctx, device_alloc(&ctx->prow, sizeof(int16_t) * prow.size()), "cudaMalloc prow") ||
+        !cuda_ok(ctx, device_alloc(&ctx->Mp, sizeof(float2) * (size_t)nclass * ctx->nci * S), "cudaMalloc Mp"))
+      return HERMITE_ERR_ALLOC;
+    if (!cuda_ok(ctx, cudaMemcpy(ctx->prow, prow.data(), sizeof(int16_t) * prow.size(), cudaMemcpyHostToDevice),
+                 "prow copy"))
+      return HERMITE_ERR_CUDA;
+    split_operator_kernel<<<64, 256, 0, ctx->stream>>>(ctx->M, ctx->nci, ctx->prow, nclass, S, ctx->Mp);
+  }
+  ctx->pslots = S;
+  ctx->psplit = P;
+  if (!cuda_ok(ctx, cudaMemcpy(ctx->pcls, cls.data(), cls.size(), cudaMemcpyHostToDevice), "pcls copy") ||
+      !cuda_ok(ctx, cudaGetLastError(), "split_operator_kernel") ||
       !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "split operator sync"))
     return HERMITE_ERR_CUDA;
   return HERMITE_OK;
