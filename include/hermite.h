@@ -151,7 +151,9 @@ int hermite_set_grid(hermite_ctx *ctx, int grid, const double *u, const double *
 int hermite_get_grid_device(hermite_ctx *ctx, int grid, double *u, double *v);
 
 /* Energies of the latest level (Sec. 3.2, 3.3, 4.2), exact per-cell
- * quadrature of the piecewise interpolants, FP64 device reduction:
+ * quadrature of the piecewise interpolants, reduced on the device in the
+ * context's arithmetic (FP64, or hi + lo FP32 pairs for split contexts) with
+ * FP64 block sums:
  *   dissipative  out[0] = int v^2 + c^2 |grad u|^2 over the domain
  *                out[1] = c^2 sum_i |d_i I^(i) u|^2_{m,..,m} + |I_{m-1} v|^2_{m,..,m}
  *                         (Eq. stable1 for d = 1, the left side of Eq. stable2

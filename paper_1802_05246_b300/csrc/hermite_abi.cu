@@ -83,6 +83,8 @@ void release(hermite_ctx *ctx) {
   if (ctx->Mp != ctx->Mc) cudaFree(ctx->Mp);
   if (ctx->prow != ctx->outrow) cudaFree(ctx->prow);
   cudaFree(ctx->pcls);
+  cudaFree(ctx->tpm);
+  cudaFree(ctx->tpmf);
 }
 
 bool is_split(const hermite_ctx *ctx) { return ctx->precision == HERMITE_SPLIT32; }
@@ -313,6 +315,7 @@ int create_context(int d, int m, int64_t N, double c, double h, double dt, int v
     if (rc == HERMITE_OK) rc = build_split_forms(ctx);
     if (cons) alloc((void **)&ctx->fscratch, sizeof(float2) * ctx->Nu * maxld, "split scratch");
   }
+  if (rc == HERMITE_OK && with_energy) rc = build_energy_tp(ctx);
   if (rc == HERMITE_OK && !cuda_ok(ctx, cudaDeviceSynchronize(), "create sync")) rc = HERMITE_ERR_CUDA;
   if (rc != HERMITE_OK) {
     g_create_error = ctx->err.empty() ? "hermite_create failed" : ctx->err;
@@ -442,8 +445,11 @@ int hermite_energy(hermite_ctx *ctx, double out[3]) {
     // split contexts reduce their hi + lo levels in the same arithmetic
     if (!is_cons(ctx)) {
       const int g = newest_grid(ctx);
-      rc = launch_energy_form_split(ctx, 0, g, ctx->fgrid[g], ctx->fgrid[g], ctx->result + 0);
-      if (!rc) rc = launch_energy_form_split(ctx, 1, g, ctx->fgrid[g], ctx->fgrid[g], ctx->result + 1);
+      rc = launch_energy_tp(ctx, g, ctx->result);
+      if (rc == HERMITE_ERR_UNSUPPORTED) {
+        rc = launch_energy_form_split(ctx, 0, g, ctx->fgrid[g], ctx->fgrid[g], ctx->result + 0);
+        if (!rc) rc = launch_energy_form_split(ctx, 1, g, ctx->fgrid[g], ctx->fgrid[g], ctx->result + 1);
+      }
     } else {
       const int gnew = newest_grid(ctx), gold = 1 - gnew;
       const size_t bytes = sizeof(float2) * ctx->Nu * ctx->ld[gold];
@@ -458,8 +464,11 @@ int hermite_energy(hermite_ctx *ctx, double out[3]) {
     }
   } else if (!is_cons(ctx)) {
     const int g = newest_grid(ctx);
-    rc = launch_energy_form(ctx, 0, g, ctx->grid[g], ctx->grid[g], ctx->result + 0);
-    if (!rc) rc = launch_energy_form(ctx, 1, g, ctx->grid[g], ctx->grid[g], ctx->result + 1);
+    rc = launch_energy_tp(ctx, g, ctx->result);
+    if (rc == HERMITE_ERR_UNSUPPORTED) {
+      rc = launch_energy_form(ctx, 0, g, ctx->grid[g], ctx->grid[g], ctx->result + 0);
+      if (!rc) rc = launch_energy_form(ctx, 1, g, ctx->grid[g], ctx->grid[g], ctx->result + 1);
+    }
   } else {
     // G = |p_new|^2 - <p_next, p_old>: p_next is the tentative update of the
     // older level's grid, formed in the scratch grid

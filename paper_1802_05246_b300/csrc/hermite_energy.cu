@@ -388,6 +388,9 @@ extern "C" int hermite_energy_noalloc(hermite_ctx *ctx, int grid, const double *
   }
   double *partials = noalloc_scratch(ctx, dev);
   if (!partials) return HERMITE_ERR_CUDA;
+  // dissipative contexts: the sum-factorised kernel, both forms in one pass
+  const int tp = launch_energy_tp_level(ctx, grid, level, ld, partials, kNoAllocPartials, out_dev);
+  if (tp != HERMITE_ERR_UNSUPPORTED) return tp;
   Geometry g = make_geometry(ctx, 1 - grid);
   g.ld_src = ld;
   for (int f = 0; f < kNumForms; ++f) {

@@ -80,6 +80,9 @@ struct hermite_ctx {
   int16_t *prow = nullptr;     // [2^d][pslots] output row of each slot (-1 unused)
   int8_t *pcls = nullptr;      // [2^d][2]
   int pslots = 0, psplit = 0;
+  // 1-D matrices of the sum-factorised dissipative energies (two class bits)
+  double *tpm = nullptr;
+  float2 *tpmf = nullptr;
   std::string err;
 };
 
@@ -112,6 +115,15 @@ int launch_half_step_split_into(hermite_ctx *ctx, int dst, const float2 *src, fl
 // Energy reduction (hermite_energy.cu).
 int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const double *B,
                        double *result_slot);
+// Sum-factorised dissipative energies (hermite_energy_tp.cu): both forms of
+// the level held on `grid` into out[0..1]; HERMITE_ERR_UNSUPPORTED when the
+// context has no tensor-product matrices (conservative, or m out of range).
+int build_energy_tp(hermite_ctx *ctx);
+int launch_energy_tp(hermite_ctx *ctx, int grid, double *out);
+// the same on a caller's FP64 coefficient-major level (plane stride ld) with
+// the given partial-sum scratch (at least 2 x 1184 doubles)
+int launch_energy_tp_level(hermite_ctx *ctx, int grid, const double *level, int64_t ld, double *partials,
+                           int64_t partials_len, double *out);
 
 Geometry make_geometry(const hermite_ctx *ctx, int dst);
 int create_context(int d, int m, int64_t N, double c, double h, double dt, int variant, int bc, int precision,

@@ -199,7 +199,10 @@ def test_dirichlet_standing_wave_even_coefficients(hb, orc):
 
 # -------------------------------------------------------------- energies
 @pytest.mark.parametrize("d,m,N,variant,bc", [(1, 3, 16, 0, 0), (2, 2, 8, 0, 0), (2, 3, 6, 2, 0),
-                                              (3, 1, 5, 0, 0), (1, 2, 9, 0, 1), (2, 2, 5, 0, 2)])
+                                              (3, 1, 5, 0, 0), (1, 2, 9, 0, 1), (2, 2, 5, 0, 2),
+                                              (3, 2, 4, 0, 0), (3, 3, 3, 0, 0), (3, 3, 3, 2, 1), (3, 2, 3, 0, 2),
+                                              (2, 4, 5, 0, 1), (1, 4, 11, 2, 2), (2, 5, 4, 0, 0),
+                                              (2, 6, 3, 2, 1), (1, 8, 7, 0, 0)])
 def test_dissipative_energy_parity(hb, orc, d, m, N, variant, bc):
     g, P = _make(hb, orc, d, m, N, 0.9, variant, bc)
     rng = np.random.default_rng(3)
@@ -210,7 +213,7 @@ def test_dissipative_energy_parity(hb, orc, d, m, N, variant, bc):
         grid = k % 2
         gu, gv = g.get_grid(grid)
         oe = P.diss_energy(grid, gu, gv)
-        np.testing.assert_allclose(e[:2], oe, rtol=1e-12)
+        np.testing.assert_allclose(e[:2], oe, rtol=max(1e-12, 10 * _oracle_tol(m)))
         g.advance_half(1)
 
 

@@ -114,3 +114,30 @@ def test_split_energies_conservative_and_boundaries(hb, d, m, N, bc):
             g.advance_half(3)
             outs.append(g.energy())
         np.testing.assert_allclose(outs[1][:2], outs[0][:2], rtol=1e-10)
+
+
+@pytest.mark.parametrize("d,m,N", [(3, 3, 40), (3, 2, 48), (2, 4, 160)])
+def test_split_energies_nonnegative_on_smooth_data(hb, d, m, N):
+    """On smooth data at fine resolution the invariant (seminorm) energy is a
+    sum of squares of nearly cancelling combinations, i.e. of rounding noise.
+    Being a sum of squares it cannot be negative, in either arithmetic; the
+    plain energy (no cancellation) agrees between the two."""
+    h = 1.0 / N
+    if d == 3:
+        cen, wid, amp = I.pulses_3d_config(0)
+        u0 = I.gaussian_data(d, m, N, h, 0, 0, cen, wid, amp)
+    else:
+        u0 = I.sine_data(d, m, N, h, 0, 0, [2 * np.pi, 4 * np.pi])
+    out = []
+    for prec in (hb.FP64, hb.SPLIT32):
+        g = hb.Hermite(d, m, N, 1.0, h, 0.9 * h, 0, 0, precision=prec)
+        g.set_state(u0, np.zeros((N ** d, m ** d)))
+        es = []
+        for _ in range(3):
+            g.step(2)
+            es.append(g.energy())
+        es = np.array(es)
+        assert np.all(es[:, 0] > 0) and np.all(es[:, 1] >= 0), (prec, es)
+        out.append(es)
+        g.close()
+    np.testing.assert_allclose(out[1][:, 0], out[0][:, 0], rtol=1e-9)
