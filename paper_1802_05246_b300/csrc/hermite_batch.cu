@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "hermite_device.cuh"
 #include "hermite_internal.h"
 
 namespace hermite {
@@ -26,64 +27,12 @@ struct BatchDesc {
   const void *src;
   void *dst;
   const double *M;
-  const float2 *Mc;
-  const int16_t *outrow;
-  const int8_t *npc;
+  const float2 *Mp;     // split operator in the context's slot layout
+  const int16_t *prow;  // output row of each slot (-1 unused)
+  const int8_t *pcls;   // parity classes of each warp's two slot ranges
   const int8_t *par;
   int nci, nco, sub;
 };
-
-template <int D>
-__device__ __forceinline__ void b_corners(const Geometry &g, int64_t t, int64_t *idx, int *gmask) {
-  int64_t ti[D];
-  int64_t r = t;
-#pragma unroll
-  for (int i = D - 1; i >= 0; --i) {
-    ti[i] = r % g.n_dst;
-    r /= g.n_dst;
-  }
-  int64_t si[D][2];
-  int gh[D][2];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int64_t s = g.dst == 1 ? ti[i] + b : ti[i] - 1 + b;
-      int ghost = 0;
-      if (g.bc == HERMITE_PERIODIC) {
-        if (s < 0) s += g.n_src;
-        if (s >= g.n_src) s -= g.n_src;
-      } else if (s < 0) {
-        s = 0;
-        ghost = 1;
-      } else if (s >= g.n_src) {
-        s = g.n_src - 1;
-        ghost = 1;
-      }
-      si[i][b] = s;
-      gh[i][b] = ghost;
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < (1 << D); ++s) {
-    int64_t id = 0;
-    int mask = 0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const int bit = (s >> (D - 1 - i)) & 1;
-      id = id * g.n_src + si[i][bit];
-      if (gh[i][bit]) mask |= 1 << (D - 1 - i);
-    }
-    idx[s] = id;
-    gmask[s] = mask;
-  }
-}
-
-__device__ __forceinline__ bool b_negates(int bc, int mask, int pb) {
-  int neg = __popc(mask & pb) & 1;
-  if (bc == HERMITE_DIRICHLET) neg ^= __popc(mask) & 1;
-  return neg != 0;
-}
 
 // ---------------------------------------------------------------- FP64
 constexpr int kBT = 128;
@@ -109,7 +58,7 @@ __global__ void __launch_bounds__(kBT) batch_f64_kernel(const BatchDesc *__restr
     for (int64_t t = I.n0 + threadIdx.x; t < I.n1; t += kBT) {
       int64_t idx[NC];
       int gm[NC];
-      b_corners<D>(P.g, t, idx, gm);
+      dev::cell_corners<D>(P.g, t, idx, gm);
       for (int c0 = 0; c0 < P.nco; c0 += CH) {
         double acc[CH];
         int po[CH];
@@ -125,7 +74,7 @@ __global__ void __launch_bounds__(kBT) batch_f64_kernel(const BatchDesc *__restr
 #pragma unroll
           for (int s = 0; s < NC; ++s) {
             double v = __ldg(plane + idx[s]);
-            if (gm[s] && b_negates(P.g.bc, gm[s], pb)) v = -v;
+            if (gm[s] && dev::ghost_negates(P.g.bc, gm[s], pb)) v = -v;
             x[s] = v;
           }
 #pragma unroll
@@ -157,33 +106,10 @@ __global__ void __launch_bounds__(kBT) batch_f64_kernel(const BatchDesc *__restr
 }
 
 // ---------------------------------------------------------------- split
-__device__ __forceinline__ float2 b_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
-}
-__device__ __forceinline__ float2 b_df_add(float2 a, float2 b) {
-  float2 t = b_two_sum(a.x, b.x);
-  t.y = __fadd_rn(t.y, __fadd_rn(a.y, b.y));
-  return t;
-}
-__device__ __forceinline__ float2 b_df_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 b_df_norm(float2 a) {
-  const float s = __fadd_rn(a.x, a.y);
-  return make_float2(s, __fsub_rn(a.y, __fsub_rn(s, a.x)));
-}
-__device__ __forceinline__ void b_df_fma(float2 &acc, const float2 m, const float2 y) {
-  const float p = __fmul_rn(m.x, y.x);
-  const float e = __fmaf_rn(m.x, y.x, -p);
-  const float2 s = b_two_sum(acc.x, p);
-  float c = __fadd_rn(acc.y, __fadd_rn(s.y, e));
-  c = __fmaf_rn(m.x, y.y, c);
-  c = __fmaf_rn(m.y, y.x, c);
-  acc = make_float2(s.x, c);
-}
-
-// one item = a range of target nodes processed 32 at a time by 2^d class warps
-template <int D, int NOMAX>
+// one item = a range of target nodes processed 32 at a time by 2^d warps;
+// warp w accumulates NS output slots, the first NP of parity class pcls[2w]
+// and the rest of class pcls[2w+1] (the contexts' slot layout)
+template <int D, int NS, int NP>
 __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *__restrict__ descs,
                                                               const BatchItem *__restrict__ items, int nitems,
                                                               unsigned *counter) {
@@ -201,14 +127,14 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
     const BatchDesc P = descs[I.prob];
     const float2 *src = static_cast<const float2 *>(P.src);
     float2 *dst = static_cast<float2 *>(P.dst);
-    const int np = P.npc[w];
+    const int cA = P.pcls[2 * w], cB = P.pcls[2 * w + 1];
     for (int64_t base = I.n0; base < I.n1; base += 32) {
       const int64_t t = base + lane;
       const bool valid = t < I.n1;
       int64_t idx[NC];
       int gm[NC];
       if (valid) {
-        b_corners<D>(P.g, t, idx, gm);
+        dev::cell_corners<D>(P.g, t, idx, gm);
       } else {
 #pragma unroll
         for (int s = 0; s < NC; ++s) {
@@ -216,9 +142,9 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
           gm[s] = 0;
         }
       }
-      float2 acc[NOMAX];
+      float2 acc[NS];
 #pragma unroll
-      for (int j = 0; j < NOMAX; ++j) acc[j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < NS; ++j) acc[j] = make_float2(0.f, 0.f);
       for (int b0 = 0; b0 < P.nci; b0 += NC) {
         const int b = b0 + w;
         if (b < P.nci) {
@@ -228,7 +154,7 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
 #pragma unroll
           for (int s = 0; s < NC; ++s) {
             float2 v = plane[idx[s]];
-            if (gm[s] && b_negates(P.g.bc, gm[s], pb)) v = b_df_neg(v);
+            if (gm[s] && dev::ghost_negates(P.g.bc, gm[s], pb)) v = dev::df_neg(v);
             x[s] = v;
           }
 #pragma unroll
@@ -237,8 +163,8 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
             for (int i = 0; i < NC; ++i)
               if (!(i & bm)) {
                 const float2 a = x[i], c = x[i | bm];
-                x[i] = b_df_add(a, c);
-                x[i | bm] = b_df_add(a, b_df_neg(c));
+                x[i] = dev::df_add(a, c);
+                x[i | bm] = dev::df_add(a, dev::df_neg(c));
               }
 #pragma unroll
           for (int q = 0; q < NC; ++q) Y[(w * NC + q) * 32 + lane] = x[q];
@@ -247,25 +173,27 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
         const int kmax = min(NC, P.nci - b0);
         for (int k = 0; k < kmax; ++k) {
           const int bb = b0 + k;
-          const float2 y = Y[(k * NC + (w ^ P.par[bb])) * 32 + lane];
-          const float4 *mrow = reinterpret_cast<const float4 *>(P.Mc + ((size_t)w * P.nci + bb) * NOMAX);
+          const int pb = P.par[bb];
+          const float2 ya = Y[(k * NC + (cA ^ pb)) * 32 + lane];
+          const float2 yb = NP < NS ? Y[(k * NC + (cB ^ pb)) * 32 + lane] : ya;
+          const float4 *mrow = reinterpret_cast<const float4 *>(P.Mp + ((size_t)w * P.nci + bb) * NS);
 #pragma unroll
-          for (int j = 0; j < NOMAX / 2; ++j) {
+          for (int j = 0; j < NS / 2; ++j) {
             const float4 mm = __ldg(mrow + j);
-            b_df_fma(acc[2 * j], make_float2(mm.x, mm.y), y);
-            b_df_fma(acc[2 * j + 1], make_float2(mm.z, mm.w), y);
+            dev::df_fma(acc[2 * j], make_float2(mm.x, mm.y), 2 * j < NP ? ya : yb);
+            dev::df_fma(acc[2 * j + 1], make_float2(mm.z, mm.w), 2 * j + 1 < NP ? ya : yb);
           }
         }
         __syncthreads();
       }
       if (valid) {
 #pragma unroll
-        for (int j = 0; j < NOMAX; ++j) {
-          if (j < np) {
-            const int row = P.outrow[w * NOMAX + j];
+        for (int j = 0; j < NS; ++j) {
+          const int row = P.prow[w * NS + j];
+          if (row >= 0) {
             float2 *o = dst + (size_t)row * P.g.ld_dst + t;
-            float2 r = b_df_norm(acc[j]);
-            if (P.sub) r = b_df_norm(b_df_add(r, b_df_neg(*o)));
+            float2 r = dev::df_norm(acc[j]);
+            if (P.sub) r = dev::df_norm(dev::df_add(r, dev::df_neg(*o)));
             *o = r;
           }
         }
@@ -283,7 +211,7 @@ struct hermite_batch {
   cudaStream_t stream = nullptr;
   hermite::BatchDesc *d_desc[2] = {nullptr, nullptr};
   struct Group {
-    int tmpl;  // CH (FP64) or NOMAX (split)
+    int tmpl;  // CH (FP64), or 64 * slots + split (split)
     hermite::BatchItem *d_items;
     int nitems;
   };
@@ -325,7 +253,7 @@ void free_items(hermite_batch *b) {
 }
 
 int group_key(const hermite_batch *b, const hermite_ctx *ctx) {
-  if (b->precision == HERMITE_SPLIT32) return ctx->nomax;
+  if (b->precision == HERMITE_SPLIT32) return ctx->pslots * 64 + ctx->psplit;
   return ctx->nco <= 8 ? 8 : (ctx->nco <= 16 ? 16 : (ctx->nco <= 32 ? 32 : 48));
 }
 
@@ -394,9 +322,9 @@ int build_descs(hermite_batch *b) {
         ds.dst = c->grid[dst];
       }
       ds.M = c->M;
-      ds.Mc = c->Mc;
-      ds.outrow = c->outrow;
-      ds.npc = c->npc;
+      ds.Mp = c->Mp;
+      ds.prow = c->prow;
+      ds.pcls = c->pcls;
       ds.par = c->par_in;
       ds.nci = c->nci;
       ds.nco = c->nco;
@@ -414,20 +342,40 @@ template <int D>
 int launch_group(hermite_batch *b, int k, const hermite_batch::Group &gr, unsigned *counter) {
   const unsigned blocks = (unsigned)(b->nsm * b->blocks_per_sm);
   if (b->precision == HERMITE_SPLIT32) {
-    // the template must equal the contexts' slot count: it is the stride of their split operators
-    switch (gr.tmpl) {
-      case 2: batch_split_kernel<D, 2><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 4: batch_split_kernel<D, 4><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 6: batch_split_kernel<D, 6><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 8: batch_split_kernel<D, 8><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 10: batch_split_kernel<D, 10><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 12: batch_split_kernel<D, 12><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 14: batch_split_kernel<D, 14><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 16: batch_split_kernel<D, 16><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 24: batch_split_kernel<D, 24><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 32: batch_split_kernel<D, 32><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      default: return HERMITE_ERR_ARG;
+    // the template must equal the contexts' slot layout: it is the stride of their split operators
+#define HERMITE_BATCH_LAYOUT(S_, P_)                                                                          \
+  if (gr.tmpl == S_ * 64 + P_) {                                                                              \
+    batch_split_kernel<D, S_, P_><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems,     \
+                                                                     counter);                                \
+    return bok(b, cudaGetLastError(), "batch kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;                      \
+  }
+    HERMITE_BATCH_LAYOUT(2, 2)
+    HERMITE_BATCH_LAYOUT(4, 4)
+    HERMITE_BATCH_LAYOUT(6, 6)
+    HERMITE_BATCH_LAYOUT(8, 8)
+    HERMITE_BATCH_LAYOUT(10, 10)
+    HERMITE_BATCH_LAYOUT(12, 12)
+    HERMITE_BATCH_LAYOUT(14, 14)
+    HERMITE_BATCH_LAYOUT(16, 16)
+    HERMITE_BATCH_LAYOUT(20, 20)
+    HERMITE_BATCH_LAYOUT(24, 24)
+    HERMITE_BATCH_LAYOUT(28, 28)
+    HERMITE_BATCH_LAYOUT(32, 32)
+    if constexpr (D > 1) {
+      HERMITE_BATCH_LAYOUT(4, 2)
+      HERMITE_BATCH_LAYOUT(6, 4)
+      HERMITE_BATCH_LAYOUT(8, 6)
+      HERMITE_BATCH_LAYOUT(10, 8)
+      HERMITE_BATCH_LAYOUT(12, 10)
+      HERMITE_BATCH_LAYOUT(14, 12)
+      HERMITE_BATCH_LAYOUT(16, 14)
+      HERMITE_BATCH_LAYOUT(20, 16)
+      HERMITE_BATCH_LAYOUT(24, 20)
+      HERMITE_BATCH_LAYOUT(28, 24)
+      HERMITE_BATCH_LAYOUT(32, 28)
     }
+#undef HERMITE_BATCH_LAYOUT
+    return HERMITE_ERR_ARG;
   } else {
     switch (gr.tmpl) {
       case 8: batch_f64_kernel<D, 8><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;

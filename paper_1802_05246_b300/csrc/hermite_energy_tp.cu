@@ -554,8 +554,12 @@ std::vector<double> tp_matrices(int m) {
 
 }  // namespace
 
+bool energy_tp_supported(int d, int m, int variant) {
+  return variant != HERMITE_CONSERVATIVE && tp_supported(d, m);
+}
+
 int build_energy_tp(hermite_ctx *ctx) {
-  if (ctx->variant == HERMITE_CONSERVATIVE || !tp_supported(ctx->d, ctx->m)) return HERMITE_OK;
+  if (!energy_tp_supported(ctx->d, ctx->m, ctx->variant)) return HERMITE_OK;
   const std::vector<double> h = tp_matrices(ctx->m);
   if (h.empty()) {
     ctx->err = "energy mass matrix not positive definite";

@@ -118,6 +118,7 @@ int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const
 // Sum-factorised dissipative energies (hermite_energy_tp.cu): both forms of
 // the level held on `grid` into out[0..1]; HERMITE_ERR_UNSUPPORTED when the
 // context has no tensor-product matrices (conservative, or m out of range).
+bool energy_tp_supported(int d, int m, int variant);
 int build_energy_tp(hermite_ctx *ctx);
 int launch_energy_tp(hermite_ctx *ctx, int grid, double *out);
 // the same on a caller's FP64 coefficient-major level (plane stride ld) with

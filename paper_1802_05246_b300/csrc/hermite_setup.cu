@@ -620,6 +620,21 @@ int build_operator(hermite_ctx *ctx, bool startup, double *out, int rows, int co
 int build_energy_forms(hermite_ctx *ctx) {
   const bool cons = ctx->variant == HERMITE_CONSERVATIVE;
   const int kinds[2] = {cons ? kConsSemi : kDissPlain, cons ? kConsGrad : kDissInvariant};
+  {
+    // physical scale of each form (xi-integrals times powers of h and c)
+    const int d = ctx->d, m = ctx->m;
+    const double hd = pow(ctx->h, (double)d), c2 = ctx->c * ctx->c;
+    for (int f = 0; f < kNumForms; ++f) {
+      if (kinds[f] == kDissPlain || kinds[f] == kConsGrad)
+        ctx->formscale[f] = c2 * hd / (ctx->h * ctx->h);
+      else if (kinds[f] == kDissInvariant)
+        ctx->formscale[f] = c2 * hd * pow(ctx->h, -2.0 * (d * m + 1));
+      else
+        ctx->formscale[f] = hd * pow(ctx->h, -2.0 * d * (m + 1));
+    }
+  }
+  // the sum-factorised kernel covers these energies without the class forms
+  if (energy_tp_supported(ctx->d, ctx->m, ctx->variant)) return HERMITE_OK;
   Basis bs;
   int rc = make_basis(ctx, bs);
   if (rc) {
@@ -629,7 +644,6 @@ int build_energy_forms(hermite_ctx *ctx) {
   const PolySpace P = make_space(ctx, bs);
   const int nclass = 1 << ctx->d;
   const int nq = cons ? ctx->Nu : ctx->Nu + ctx->Nv;
-  const double hd = pow(ctx->h, (double)ctx->d), c2 = ctx->c * ctx->c;
   for (int f = 0; f < kNumForms && rc == HERMITE_OK; ++f) {
     const int kind = kinds[f];
     const int ncomp = (kind == kConsSemi) ? 1 : (kind == kConsGrad ? ctx->d : ctx->d + 1);
@@ -662,14 +676,6 @@ int build_energy_forms(hermite_ctx *ctx) {
           !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "energy form sync"))
         rc = HERMITE_ERR_CUDA;
       ctx->nq[f] = nq;
-      // physical scale of each form (xi-integrals times powers of h and c)
-      const int d = ctx->d, m = ctx->m;
-      if (kind == kDissPlain || kind == kConsGrad)
-        ctx->formscale[f] = c2 * hd / (ctx->h * ctx->h);
-      else if (kind == kDissInvariant)
-        ctx->formscale[f] = c2 * hd * pow(ctx->h, -2.0 * (d * m + 1));
-      else
-        ctx->formscale[f] = hd * pow(ctx->h, -2.0 * d * (m + 1));
       if (rc == HERMITE_OK) rc = build_lowrank_factor(ctx, f, F, nclass, nq, ncomp, P);
     }
     cudaFree(F);

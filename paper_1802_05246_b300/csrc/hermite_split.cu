@@ -43,7 +43,8 @@ __device__ __forceinline__ void half_step_split_body(
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < NC * nci * S; i += NT) Ms[i] = Mp[i];
   for (int i = threadIdx.x; i < nci; i += NT) pin[i] = par[i];
-  const int cA = pcls[2 * w], cB = pcls[2 * w + 1];
+  // one class per warp (P = S): warp w holds class w
+  const int cA = P == S ? w : pcls[2 * w], cB = P == S ? w : pcls[2 * w + 1];
   __syncthreads();
   const int64_t nblk = (g.nodes_dst + 31) / 32;
   const int nchunks = (nci + NC - 1) / NC;
