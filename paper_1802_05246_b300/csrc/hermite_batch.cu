@@ -113,6 +113,7 @@ template <int D, int NS, int NP>
 __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *__restrict__ descs,
                                                               const BatchItem *__restrict__ items, int nitems,
                                                               unsigned *counter) {
+  static_assert(NS % 2 == 0 && NP % 2 == 0, "slot pairs never straddle the two classes");
   constexpr int NC = 1 << D;
   __shared__ float2 Y[NC * NC * 32];
   __shared__ int item_s;
@@ -142,9 +143,10 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
           gm[s] = 0;
         }
       }
-      float2 acc[NS];
+      // slot pairs (2k, 2k+1): hi parts in ahi[k], lo parts in alo[k]
+      float2 ahi[NS / 2], alo[NS / 2];
 #pragma unroll
-      for (int j = 0; j < NS; ++j) acc[j] = make_float2(0.f, 0.f);
+      for (int k = 0; k < NS / 2; ++k) ahi[k] = alo[k] = make_float2(0.f, 0.f);
       for (int b0 = 0; b0 < P.nci; b0 += NC) {
         const int b = b0 + w;
         if (b < P.nci) {
@@ -176,12 +178,28 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
           const int pb = P.par[bb];
           const float2 ya = Y[(k * NC + (cA ^ pb)) * 32 + lane];
           const float2 yb = NP < NS ? Y[(k * NC + (cB ^ pb)) * 32 + lane] : ya;
+          const float2 yah = make_float2(ya.x, ya.x), yal = make_float2(ya.y, ya.y), yan = make_float2(-ya.x, -ya.x);
+          const float2 ybh = make_float2(yb.x, yb.x), ybl = make_float2(yb.y, yb.y), ybn = make_float2(-yb.x, -yb.x);
           const float4 *mrow = reinterpret_cast<const float4 *>(P.Mp + ((size_t)w * P.nci + bb) * NS);
 #pragma unroll
           for (int j = 0; j < NS / 2; ++j) {
-            const float4 mm = __ldg(mrow + j);
-            dev::df_fma(acc[2 * j], make_float2(mm.x, mm.y), 2 * j < NP ? ya : yb);
-            dev::df_fma(acc[2 * j + 1], make_float2(mm.z, mm.w), 2 * j + 1 < NP ? ya : yb);
+            const float4 mm = __ldg(mrow + j);  // (hi, hi, lo, lo) of slots 2j, 2j+1
+            if constexpr (NS >= 24 || NS == 2) {
+              // measured: with 24 or more slots the packed pairs ran far slower
+              // in this kernel (operator rows from global memory) than the
+              // scalar form, and with one slot pair forming the packed copies
+              // of y costs what the packing saves; these layouts keep the
+              // scalar form
+              float2 a0 = make_float2(ahi[j].x, alo[j].x), a1 = make_float2(ahi[j].y, alo[j].y);
+              dev::df_fma(a0, make_float2(mm.x, mm.z), 2 * j < NP ? ya : yb);
+              dev::df_fma(a1, make_float2(mm.y, mm.w), 2 * j < NP ? ya : yb);
+              ahi[j] = make_float2(a0.x, a1.x);
+              alo[j] = make_float2(a0.y, a1.y);
+            } else if (2 * j < NP) {
+              dev::df_fma_x2(ahi[j], alo[j], make_float2(mm.x, mm.y), make_float2(mm.z, mm.w), yah, yal, yan);
+            } else {
+              dev::df_fma_x2(ahi[j], alo[j], make_float2(mm.x, mm.y), make_float2(mm.z, mm.w), ybh, ybl, ybn);
+            }
           }
         }
         __syncthreads();
@@ -192,7 +210,8 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
           const int row = P.prow[w * NS + j];
           if (row >= 0) {
             float2 *o = dst + (size_t)row * P.g.ld_dst + t;
-            float2 r = dev::df_norm(acc[j]);
+            const float2 a = (j & 1) ? make_float2(ahi[j / 2].y, alo[j / 2].y) : make_float2(ahi[j / 2].x, alo[j / 2].x);
+            float2 r = dev::df_norm(a);
             if (P.sub) r = dev::df_norm(dev::df_add(r, dev::df_neg(*o)));
             *o = r;
           }

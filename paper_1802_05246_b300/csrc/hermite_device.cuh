@@ -41,6 +41,29 @@ __device__ __forceinline__ void df_fma(float2 &acc, const float2 m, const float2
   acc = make_float2(s.x, c);
 }
 
+// Two accumulators at once, (ahi, alo) holding slots (j, j+1) as hi and lo
+// pairs: acc += m * y for both, with the operations of df_fma on packed FP32
+// pairs (one instruction for the two slots; the same roundings, so the same
+// results).  y is shared: yhi = (y.x, y.x), ylo = (y.y, y.y), nyhi = -yhi.
+// A difference u - v is formed as fma(v, -1, u), which rounds like u - v.
+__device__ __forceinline__ void df_fma_x2(float2 &ahi, float2 &alo, const float2 mhi, const float2 mlo,
+                                          const float2 yhi, const float2 ylo, const float2 nyhi) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 pn = __fmul2_rn(mhi, nyhi);    // -p, p = fl(m.hi y.hi)
+  const float2 e = __ffma2_rn(mhi, yhi, pn);  // m.hi y.hi - p, exact
+  const float2 s = __ffma2_rn(pn, m1, ahi);   // fl(a + p)
+  const float2 bb = __ffma2_rn(ahi, m1, s);   // fl(s - a)
+  const float2 t1 = __ffma2_rn(bb, m1, s);    // fl(s - bb)
+  const float2 t2 = __ffma2_rn(t1, m1, ahi);  // fl(a - (s - bb))
+  const float2 t3 = __fadd2_rn(pn, bb);       // -fl(p - bb)
+  const float2 err = __ffma2_rn(t3, m1, t2);  // rounding error of a + p
+  float2 c = __fadd2_rn(alo, __fadd2_rn(err, e));
+  c = __ffma2_rn(mhi, ylo, c);
+  c = __ffma2_rn(mlo, yhi, c);
+  ahi = s;
+  alo = c;
+}
+
 // a * b with the same three split products, normalised
 __device__ __forceinline__ float2 df_mul(const float2 a, const float2 b) {
   const float p = __fmul_rn(a.x, b.x);

@@ -32,7 +32,7 @@ __device__ __forceinline__ void half_step_split_body(
     const Geometry &g, const float2 *__restrict__ Mp, const int16_t *__restrict__ prow,
     const int8_t *__restrict__ pcls, int nci, const int8_t *__restrict__ par, const float2 *__restrict__ src,
     float2 *__restrict__ dst, int subtract_old) {
-  static_assert(S % 2 == 0 && P > 0 && P <= S, "slot layout");
+  static_assert(S % 2 == 0 && P % 2 == 0 && P > 0 && P <= S, "slot layout: slot pairs never straddle the classes");
   constexpr int NC = 1 << D;
   constexpr int NT = 32 * NC;
   constexpr int YSZ = NC * NC * 32;
@@ -92,9 +92,10 @@ __device__ __forceinline__ void half_step_split_body(
 #pragma unroll
       for (int q = 0; q < NC; ++q) Y[(w * NC + q) * 32 + lane] = x[q];
     };
-    float2 acc[S];
+    // slot pairs (2k, 2k+1): hi parts in ahi[k], lo parts in alo[k]
+    float2 ahi[S / 2], alo[S / 2];
 #pragma unroll
-    for (int j = 0; j < S; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int k = 0; k < S / 2; ++k) ahi[k] = alo[k] = make_float2(0.f, 0.f);
     load(0);
     transform(0, Ybuf);
     if (nchunks > 1) load(NC);
@@ -103,20 +104,33 @@ __device__ __forceinline__ void half_step_split_body(
       const float2 *Y = Ybuf + (NBUF == 2 ? (ch & 1) * YSZ : 0);
       const int b0 = ch * NC;
       const int kmax = min(NC, nci - b0);
-      // every slot runs (unused slots multiply zeros) so that the NOMAX
-      // independent accumulator chains interleave; operator pairs are read
-      // 16 bytes at a time
+      // every slot runs (unused slots multiply zeros) so that the S
+      // independent accumulator chains interleave; a slot pair's operator
+      // entries (hi, hi, lo, lo) are read 16 bytes at a time
       auto consume = [&](int k) {
         const int bb = b0 + k;
         const int pb = pin[bb];
         const float2 ya = Y[(k * NC + (cA ^ pb)) * 32 + lane];
         const float2 yb = P < S ? Y[(k * NC + (cB ^ pb)) * 32 + lane] : ya;
+        const float2 yah = make_float2(ya.x, ya.x), yal = make_float2(ya.y, ya.y), yan = make_float2(-ya.x, -ya.x);
+        const float2 ybh = make_float2(yb.x, yb.x), ybl = make_float2(yb.y, yb.y), ybn = make_float2(-yb.x, -yb.x);
         const float4 *mrow = reinterpret_cast<const float4 *>(Ms + ((size_t)w * nci + bb) * S);
 #pragma unroll
         for (int j = 0; j < S / 2; ++j) {
           const float4 mm = mrow[j];
-          df_fma(acc[2 * j], make_float2(mm.x, mm.y), 2 * j < P ? ya : yb);
-          df_fma(acc[2 * j + 1], make_float2(mm.z, mm.w), 2 * j + 1 < P ? ya : yb);
+          if constexpr (S == 2) {
+            // one slot pair: forming the packed copies of y would cost as much
+            // as the packing saves (measured), so the scalar form
+            float2 a0 = make_float2(ahi[j].x, alo[j].x), a1 = make_float2(ahi[j].y, alo[j].y);
+            df_fma(a0, make_float2(mm.x, mm.z), ya);
+            df_fma(a1, make_float2(mm.y, mm.w), ya);
+            ahi[j] = make_float2(a0.x, a1.x);
+            alo[j] = make_float2(a0.y, a1.y);
+          } else if (2 * j < P) {
+            dev::df_fma_x2(ahi[j], alo[j], make_float2(mm.x, mm.y), make_float2(mm.z, mm.w), yah, yal, yan);
+          } else {
+            dev::df_fma_x2(ahi[j], alo[j], make_float2(mm.x, mm.y), make_float2(mm.z, mm.w), ybh, ybl, ybn);
+          }
         }
       };
       if (kmax == NC) {
@@ -143,7 +157,8 @@ __device__ __forceinline__ void half_step_split_body(
         const int row = prow[w * S + j];
         if (row >= 0) {
           float2 *o = dst + (size_t)row * g.ld_dst + t;
-          float2 r = df_norm(acc[j]);
+          const float2 a = (j & 1) ? make_float2(ahi[j / 2].y, alo[j / 2].y) : make_float2(ahi[j / 2].x, alo[j / 2].x);
+          float2 r = df_norm(a);
           if (subtract_old) r = df_norm(df_add(r, df_neg(*o)));
           *o = r;
         }
@@ -172,7 +187,12 @@ __global__ void __launch_bounds__(32 << D, 2) half_step_split_1buf_kernel(
 
 template <int D, int S, int P, int NBUF>
 int launch_split_dnb(hermite_ctx *ctx, const Geometry &g, const float2 *src, float2 *dst, bool sub, size_t smem) {
-  auto kern = NBUF == 2 ? half_step_split_kernel<D, S, P> : half_step_split_1buf_kernel<D, S, P>;
+  auto kern = [] {
+    if constexpr (NBUF == 2)
+      return half_step_split_kernel<D, S, P>;
+    else
+      return half_step_split_1buf_kernel<D, S, P>;
+  }();
   static thread_local int configured_dev = -1;
   if (configured_dev != ctx->device) {
     if (!cuda_ok(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
@@ -421,10 +441,12 @@ int launch_energy_split_d(hermite_ctx *ctx, int form, int grid, const float2 *A,
   return cuda_ok(ctx, cudaGetLastError(), "energy_factored_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
-// operator rows grouped by output parity class, each entry split hi + lo
+// operator rows in a warp slot layout, each entry split hi + lo; the entries
+// of slots 2k and 2k+1 for one input are stored (hi, hi, lo, lo)
 __global__ void split_operator_kernel(const double *M, int nci, const int16_t *outrow, int nclass, int nomax,
                                       float2 *Mc) {
   const int64_t n = (int64_t)nclass * nci * nomax;
+  float *f = reinterpret_cast<float *>(Mc);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(i % nomax);
     const int b = (int)((i / nomax) % nci);
@@ -432,7 +454,9 @@ __global__ void split_operator_kernel(const double *M, int nci, const int16_t *o
     const int row = outrow[c * nomax + j];
     const double m = row >= 0 ? M[(size_t)row * nci + b] : 0.0;
     const float hi = __double2float_rn(m);
-    Mc[i] = make_float2(hi, __double2float_rn(m - (double)hi));
+    const int64_t base = 2 * (i - j) + 4 * (j / 2) + (j & 1);
+    f[base] = hi;
+    f[base + 2] = __double2float_rn(m - (double)hi);
   }
 }
 

@@ -28,6 +28,10 @@ def hb():
     (2, 6, 5, 0.8, 0, 0, 2), (1, 6, 9, 0.7, 1, 1, 6),
     # small operators (two or four slots per class warp)
     (3, 1, 5, 0.9, 1, 0, 2), (3, 1, 4, 1.0, 2, 1, 2), (2, 1, 6, 0.9, 1, 2, 3), (1, 1, 9, 1.0, 0, 0, 5),
+    # the remaining two-class slot layouts (slots, first-class slots): 3-D m = 2
+    # dissipative (6, 4) and conservative (4, 2), 2-D m = 5 dissipative (16, 14),
+    # 2-D m = 6 conservative (14, 12)
+    (3, 2, 4, 0.9, 0, 2, 2), (3, 2, 4, 0.9, 1, 0, 2), (2, 5, 5, 0.9, 0, 0, 2), (2, 6, 5, 0.9, 1, 1, 2),
 ])
 def test_split_matches_oracle(hb, orc, d, m, N, lam, variant, bc, nsteps):
     h = 1.0 / N
