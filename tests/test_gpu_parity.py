@@ -217,6 +217,27 @@ def test_dissipative_energy_parity(hb, orc, d, m, N, variant, bc):
         g.advance_half(1)
 
 
+def test_dissipative_energy_parity_many_tiles(hb, orc):
+    """A grid with more 32-cell tiles than the energy kernel's persistent
+    blocks (2-D, m = 2, 200^2 cells, Dirichlet): every block loops over several
+    tiles.  FP64 and split energies of both grids against the oracle."""
+    d, m, N = 2, 2, 200
+    rng = np.random.default_rng(11)
+    for precision, rtol in ((hb.FP64, 1e-12), (hb.SPLIT32, 1e-10)):
+        h = 1.0 / N
+        g = hb.Hermite(d, m, N, 1.0, h, 0.9 * h, 0, 1, precision=precision)
+        P = orc.Problem(d, m, N, 1.0, h, 0.9 * h, 0, 1)
+        u, v = _rand_state(rng, P.nnodes(0), P.Nu, P.Nv)
+        g.set_state(u, v)
+        for grid in (0, 1):
+            e = g.energy()
+            gu, gv = g.get_grid(grid)
+            oe = P.diss_energy(grid, gu, gv)
+            np.testing.assert_allclose(e[:2], oe, rtol=rtol)
+            g.advance_half(1)
+        g.close()
+
+
 @pytest.mark.parametrize("d,m,N,bc", [(1, 2, 12, 0), (2, 2, 6, 0), (3, 1, 5, 0), (1, 3, 9, 1), (2, 1, 5, 2)])
 def test_conservative_energy_parity_and_conservation(hb, orc, d, m, N, bc):
     g, P = _make(hb, orc, d, m, N, 0.95, 1, bc)
