@@ -436,11 +436,25 @@ int hermite_set_grid(hermite_ctx *ctx, int grid, const double *u, const double *
   return rc;
 }
 
+// Conservative energies with the sum-factorised kernel: the forms of the
+// newest level (slots 0, 1), of A + B and A - B for the tentative next level
+// A and the older level B (slots 2, 4: polarisation of their inner product),
+// and, when the newest level is the dual one, of the primal level (slot 7).
+static int cons_energies_tp(hermite_ctx *ctx, int gnew, const void *A, const void *B) {
+  const int gold = 1 - gnew;
+  int rc = launch_energy_tp(ctx, gnew, ctx->result + 0);
+  if (!rc) rc = launch_energy_tp_pair(ctx, gold, A, B, 1.0f, ctx->result + 2);
+  if (!rc) rc = launch_energy_tp_pair(ctx, gold, A, B, -1.0f, ctx->result + 4);
+  if (!rc && gnew != 0) rc = launch_energy_tp(ctx, 0, ctx->result + 6);
+  return rc;
+}
+
 int hermite_energy(hermite_ctx *ctx, double out[3]) {
   if (!ctx || !out) return ctx ? fail(ctx, HERMITE_ERR_ARG, "out is NULL") : HERMITE_ERR_ARG;
   if (!ctx->has_energy) return fail(ctx, HERMITE_ERR_STATE, "this context was created without energy forms");
   int rc = HERMITE_OK;
-  double host[4] = {0, 0, 0, 0};
+  bool cons_tp = false;
+  double host[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (is_split(ctx)) {
     // split contexts reduce their hi + lo levels in the same arithmetic
     if (!is_cons(ctx)) {
@@ -458,9 +472,14 @@ int hermite_energy(hermite_ctx *ctx, double out[3]) {
                    "copy level"))
         return HERMITE_ERR_CUDA;
       rc = launch_half_step_split_into(ctx, gold, ctx->fgrid[gnew], ctx->fscratch, true);
-      if (!rc) rc = launch_energy_form_split(ctx, 0, gnew, ctx->fgrid[gnew], ctx->fgrid[gnew], ctx->result + 0);
-      if (!rc) rc = launch_energy_form_split(ctx, 0, gold, ctx->fscratch, ctx->fgrid[gold], ctx->result + 1);
-      if (!rc) rc = launch_energy_form_split(ctx, 1, 0, ctx->fgrid[0], ctx->fgrid[0], ctx->result + 2);
+      if (!rc && ctx->tpm) {
+        rc = cons_energies_tp(ctx, gnew, ctx->fscratch, ctx->fgrid[gold]);
+        cons_tp = true;
+      } else {
+        if (!rc) rc = launch_energy_form_split(ctx, 0, gnew, ctx->fgrid[gnew], ctx->fgrid[gnew], ctx->result + 0);
+        if (!rc) rc = launch_energy_form_split(ctx, 0, gold, ctx->fscratch, ctx->fgrid[gold], ctx->result + 1);
+        if (!rc) rc = launch_energy_form_split(ctx, 1, 0, ctx->fgrid[0], ctx->fgrid[0], ctx->result + 2);
+      }
     }
   } else if (!is_cons(ctx)) {
     const int g = newest_grid(ctx);
@@ -479,16 +498,27 @@ int hermite_energy(hermite_ctx *ctx, double out[3]) {
                  "copy level"))
       return HERMITE_ERR_CUDA;
     rc = launch_half_step(ctx, gold, ctx->M, ctx->nci, ctx->nco, ctx->grid[gnew], ctx->scratch_grid, true);
-    if (!rc) rc = launch_energy_form(ctx, 0, gnew, ctx->grid[gnew], ctx->grid[gnew], ctx->result + 0);
-    if (!rc) rc = launch_energy_form(ctx, 0, gold, ctx->scratch_grid, ctx->grid[gold], ctx->result + 1);
-    if (!rc) rc = launch_energy_form(ctx, 1, 0, ctx->grid[0], ctx->grid[0], ctx->result + 2);
+    if (!rc && ctx->tpm) {
+      rc = cons_energies_tp(ctx, gnew, ctx->scratch_grid, ctx->grid[gold]);
+      cons_tp = true;
+    } else {
+      if (!rc) rc = launch_energy_form(ctx, 0, gnew, ctx->grid[gnew], ctx->grid[gnew], ctx->result + 0);
+      if (!rc) rc = launch_energy_form(ctx, 0, gold, ctx->scratch_grid, ctx->grid[gold], ctx->result + 1);
+      if (!rc) rc = launch_energy_form(ctx, 1, 0, ctx->grid[0], ctx->grid[0], ctx->result + 2);
+    }
   }
   if (rc) return rc;
-  if (!cuda_ok(ctx, cudaMemcpyAsync(host, ctx->result, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->stream),
+  if (!cuda_ok(ctx, cudaMemcpyAsync(host, ctx->result, sizeof(double) * 8, cudaMemcpyDeviceToHost, ctx->stream),
                "energy copy") ||
       !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "energy sync"))
     return HERMITE_ERR_CUDA;
-  if (is_cons(ctx)) {
+  if (cons_tp) {
+    // slots: [0,1] forms of the newest level, [2] |A+B|^2, [4] |A-B|^2 of the
+    // tentative next level A and the older level B (their inner product is
+    // the difference / 4), [1] or [7] the gradient form of the primal level
+    out[0] = newest_grid(ctx) == 0 ? host[1] : host[7];
+    out[1] = host[0] - 0.25 * (host[2] - host[4]);
+  } else if (is_cons(ctx)) {
     out[0] = host[2];
     out[1] = host[0] - host[1];
   } else {

@@ -1,5 +1,6 @@
-// Energies of the dissipative method by sum factorisation (Sec. 3.2 Eq.
-// stable1/Energyeq, Sec. 3.3 Eq. stable2), FP64 or double-FP32.
+// Energies by sum factorisation, FP64 or double-FP32: the dissipative
+// method's (Sec. 3.2 Eq. stable1/Energyeq, Sec. 3.3 Eq. stable2) and the
+// conservative method's seminorm and gradient forms (Sec. 4.2).
 //
 // In the reference coordinate xi of a cell the interpolant is a tensor
 // product of 1-D two-point Hermite bases, and after the Walsh-Hadamard
@@ -16,7 +17,8 @@
 //   invariant:  sum_ax |(R_ax x S_others) y_u restricted|^2 + |(S x S x S) y_v|^2,
 //               R^T R = G^(m+1)_{m,e}, S^T S = G^(m)_{m-1,e}, the restriction
 //               keeping orders <= m along ax and <= m-1 elsewhere (the
-//               interpolant I^(ax) of Sec. 3.3).
+//               interpolant I^(ax) of Sec. 3.3);
+//   conservative: |(R x R x R) y_u|^2 and the gradient term as above.
 // The 1-D matrices are built once per context on the host in long double.
 // A block takes 32 cells and all 2^d classes (warp = class, lane = cell):
 // its warps gather and transform the corner data into the class tensors in
@@ -167,15 +169,21 @@ __device__ __forceinline__ typename Ar::T inv_u_term(const typename Ar::T *yu, c
   return kron_norm2<Ar, D, n, E0, E1, E2, K0, K1, K2, false>(yu, A0, A1, A2, nullptr);
 }
 
-template <class Ar, int D, int MM>
+// CONS = false: the dissipative forms of the level src (plain, invariant).
+// CONS = true: the conservative forms (Sec. 4.2) of the u level
+// src + sigma * srcB, sigma in {0, 1, -1}: the seminorm |p|^2_{m+1,..,m+1}
+// and int |grad p|^2 (the bilinear form of two levels follows by
+// polarisation from sigma = +-1).
+template <class Ar, int D, int MM, bool CONS>
 __global__ void __launch_bounds__(32 << D) energy_tp_kernel(Geometry g, const typename Ar::T *__restrict__ mats,
-                                                            const typename Ar::T *__restrict__ src, double vs2,
-                                                            double *__restrict__ partials) {
+                                                            const typename Ar::T *__restrict__ src,
+                                                            const typename Ar::T *__restrict__ srcB, float sigma,
+                                                            double vs2, double *__restrict__ partials) {
   using T = typename Ar::T;
   using Sh = Shape<MM>;
   constexpr int NC = 1 << D, NT = 32 * NC;
   constexpr int n = Sh::n, nv = Sh::nv;
-  constexpr int NU = ipow(n, D), NV = ipow(nv, D), NCI = NU + NV;
+  constexpr int NU = ipow(n, D), NV = CONS ? 0 : ipow(nv, D), NCI = NU + NV;
   extern __shared__ __align__(16) unsigned char tp_smem[];
   T *ms = reinterpret_cast<T *>(tp_smem);  // [2][EB]
   T *lamsum = ms + 2 * Sh::EB;            // [NC][NU]
@@ -225,6 +233,13 @@ __global__ void __launch_bounds__(32 << D) energy_tp_kernel(Geometry g, const ty
     auto load = [&](int b, T *dst) {
 #pragma unroll
       for (int s = 0; s < NC; ++s) dst[s] = (b < NCI && valid) ? src[(size_t)b * g.ld_src + idx[s]] : Ar::zero();
+      if (CONS && sigma != 0.0f && b < NCI && valid) {
+#pragma unroll
+        for (int s = 0; s < NC; ++s) {
+          const T vb = srcB[(size_t)b * g.ld_src + idx[s]];
+          dst[s] = Ar::add(dst[s], sigma > 0.0f ? vb : Ar::neg(vb));
+        }
+      }
     };
     load(w, x);
 #pragma unroll 1
@@ -258,25 +273,41 @@ __global__ void __launch_bounds__(32 << D) energy_tp_kernel(Geometry g, const ty
     __syncthreads();
     // Phase B: this thread's (cell, class) terms
     const T *yu = Ty + (size_t)c * NCI * 32 + lane;
-    const T *yv = yu + NU * 32;
-    const T pvc = kron_norm2<Ar, D, nv, nv, nv, nv, nv, nv, nv, false>(yv, mb[0] + Sh::oF, mb[1] + Sh::oF,
-                                                                       mb[2] + Sh::oF, nullptr);
-    const T ivc = kron_norm2<Ar, D, nv, nv, nv, nv, Sh::RS, Sh::RS, Sh::RS, false>(yv, mb[0] + Sh::oS, mb[1] + Sh::oS,
-                                                                                  mb[2] + Sh::oS, nullptr);
-    T inv = inv_u_term<Ar, D, MM, 0>(yu, mb);
-    if constexpr (D > 1) inv = Ar::add(inv, inv_u_term<Ar, D, MM, 1>(yu, mb));
-    if constexpr (D > 2) inv = Ar::add(inv, inv_u_term<Ar, D, MM, 2>(yu, mb));
-    // plain u: the stiffness diagonalised along every axis, weighted by lam sums
+    // plain / gradient: the stiffness diagonalised along every axis, weighted by lam sums
     const T pl = kron_norm2<Ar, D, n, n, n, n, n, n, n, true>(yu, mb[0] + Sh::oW, mb[1] + Sh::oW, mb[2] + Sh::oW,
                                                               lamsum + c * NU);
-    pv = Ar::add(pv, Ar::scale(pvc, cw));
-    iv = Ar::add(iv, Ar::scale(ivc, cw));
-    pu = Ar::add(pu, Ar::scale(pl, cw));
-    iu = Ar::add(iu, Ar::scale(inv, cw));
+    if constexpr (CONS) {
+      // seminorm: the (m+1)-th derivative in every axis
+      const T sm = kron_norm2<Ar, D, n, n, n, n, Sh::RR, Sh::RR, Sh::RR, false>(yu, mb[0] + Sh::oR, mb[1] + Sh::oR,
+                                                                              mb[2] + Sh::oR, nullptr);
+      iu = Ar::add(iu, Ar::scale(sm, cw));
+      pu = Ar::add(pu, Ar::scale(pl, cw));
+    } else {
+      const T *yv = yu + NU * 32;
+      const T pvc = kron_norm2<Ar, D, nv, nv, nv, nv, nv, nv, nv, false>(yv, mb[0] + Sh::oF, mb[1] + Sh::oF,
+                                                                         mb[2] + Sh::oF, nullptr);
+      const T ivc = kron_norm2<Ar, D, nv, nv, nv, nv, Sh::RS, Sh::RS, Sh::RS, false>(
+          yv, mb[0] + Sh::oS, mb[1] + Sh::oS, mb[2] + Sh::oS, nullptr);
+      T inv = inv_u_term<Ar, D, MM, 0>(yu, mb);
+      if constexpr (D > 1) inv = Ar::add(inv, inv_u_term<Ar, D, MM, 1>(yu, mb));
+      if constexpr (D > 2) inv = Ar::add(inv, inv_u_term<Ar, D, MM, 2>(yu, mb));
+      pv = Ar::add(pv, Ar::scale(pvc, cw));
+      iv = Ar::add(iv, Ar::scale(ivc, cw));
+      pu = Ar::add(pu, Ar::scale(pl, cw));
+      iu = Ar::add(iu, Ar::scale(inv, cw));
+    }
     __syncthreads();  // the next tile's phase A overwrites the class tensors
   }
-  // block sums of the plain and invariant energies (v terms carry (h/c)^2)
-  double e[2] = {Ar::to_double(pu) + vs2 * Ar::to_double(pv), Ar::to_double(iu) + vs2 * Ar::to_double(iv)};
+  // block sums: dissipative [plain, invariant] (v terms carry (h/c)^2),
+  // conservative [seminorm, gradient]
+  double e[2];
+  if constexpr (CONS) {
+    e[0] = Ar::to_double(iu);
+    e[1] = Ar::to_double(pu);
+  } else {
+    e[0] = Ar::to_double(pu) + vs2 * Ar::to_double(pv);
+    e[1] = Ar::to_double(iu) + vs2 * Ar::to_double(iv);
+  }
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
     double v = e[f];
@@ -430,15 +461,15 @@ int count_parity(int lo, int hi, int e) {
 
 bool tp_supported(int d, int m) { return m >= 1 && m <= (d == 3 ? 3 : (d == 2 ? 6 : 8)); }
 
-template <class Ar, int D, int MM>
-int launch_tp(hermite_ctx *ctx, int grid, const typename Ar::T *level, int64_t ld, const typename Ar::T *mats,
-              double *partials, int64_t partials_len, double *out) {
+template <class Ar, int D, int MM, bool CONS>
+int launch_tp(hermite_ctx *ctx, int grid, const typename Ar::T *A, const typename Ar::T *B, float sigma, int64_t ld,
+              const typename Ar::T *mats, double *partials, int64_t partials_len, double *out) {
   using T = typename Ar::T;
   using Sh = Shape<MM>;
   constexpr int NC = 1 << D;
   constexpr int NU = ipow(MM + 1, D);
-  auto kern = energy_tp_kernel<Ar, D, MM>;
-  constexpr int NCI = NU + ipow(MM, D);
+  constexpr int NCI = NU + (CONS ? 0 : ipow(MM, D));
+  auto kern = energy_tp_kernel<Ar, D, MM, CONS>;
   const size_t smem = sizeof(T) * (2 * Sh::EB + NC * NU + (size_t)NC * NCI * 32);
   static thread_local int configured_dev = -1;
   if (configured_dev != ctx->device) {
@@ -453,18 +484,21 @@ int launch_tp(hermite_ctx *ctx, int grid, const typename Ar::T *level, int64_t l
   const int64_t ntiles = (g.nodes_dst + 31) / 32;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>({ntiles, 148 * 8, partials_len / 2}));
   const double vs = ctx->h / ctx->c;
-  kern<<<(unsigned)blocks, 32 * NC, smem, ctx->stream>>>(g, mats, level, vs * vs, partials);
+  kern<<<(unsigned)blocks, 32 * NC, smem, ctx->stream>>>(g, mats, A, B ? B : A, B ? sigma : 0.0f, vs * vs,
+                                                          partials);
   for (int f = 0; f < 2; ++f)
     reduce_tp_kernel<<<1, 256, 0, ctx->stream>>>(partials + f * blocks, blocks, ctx->formscale[f], out + f);
   return cuda_ok(ctx, cudaGetLastError(), "energy_tp_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
 template <class Ar>
-int launch_tp_any(hermite_ctx *ctx, int grid, const typename Ar::T *level, int64_t ld, const typename Ar::T *mats,
-                  double *partials, int64_t plen, double *out) {
-#define HERMITE_TP_CASE(D_, M_) \
-  case D_ * 8 + M_:             \
-    return launch_tp<Ar, D_, M_>(ctx, grid, level, ld, mats, partials, plen, out);
+int launch_tp_any(hermite_ctx *ctx, int grid, const typename Ar::T *A, const typename Ar::T *B, float sigma,
+                  int64_t ld, const typename Ar::T *mats, double *partials, int64_t plen, double *out) {
+  const bool cons = ctx->variant == HERMITE_CONSERVATIVE;
+#define HERMITE_TP_CASE(D_, M_)                                                                         \
+  case D_ * 8 + M_:                                                                                     \
+    return cons ? launch_tp<Ar, D_, M_, true>(ctx, grid, A, B, sigma, ld, mats, partials, plen, out)   \
+                : launch_tp<Ar, D_, M_, false>(ctx, grid, A, B, sigma, ld, mats, partials, plen, out);
   switch (ctx->d * 8 + ctx->m) {
     HERMITE_TP_CASE(1, 1)
     HERMITE_TP_CASE(1, 2)
@@ -555,7 +589,8 @@ std::vector<double> tp_matrices(int m) {
 }  // namespace
 
 bool energy_tp_supported(int d, int m, int variant) {
-  return variant != HERMITE_CONSERVATIVE && tp_supported(d, m);
+  (void)variant;  // both methods (the conservative one for m >= 1 as well)
+  return tp_supported(d, m);
 }
 
 int build_energy_tp(hermite_ctx *ctx) {
@@ -579,18 +614,24 @@ int build_energy_tp(hermite_ctx *ctx) {
 }
 
 int launch_energy_tp(hermite_ctx *ctx, int grid, double *out) {
+  return launch_energy_tp_pair(ctx, grid, nullptr, nullptr, 0.0f, out);
+}
+
+int launch_energy_tp_pair(hermite_ctx *ctx, int grid, const void *A, const void *B, float sigma, double *out) {
   if (!ctx->tpm) return HERMITE_ERR_UNSUPPORTED;
   if (ctx->precision == HERMITE_SPLIT32)
-    return launch_tp_any<ArSplit>(ctx, grid, ctx->fgrid[grid], ctx->ld[grid], ctx->tpmf, ctx->partials,
+    return launch_tp_any<ArSplit>(ctx, grid, A ? static_cast<const float2 *>(A) : ctx->fgrid[grid],
+                                  static_cast<const float2 *>(B), sigma, ctx->ld[grid], ctx->tpmf, ctx->partials,
                                   ctx->partials_len, out);
-  return launch_tp_any<ArF64>(ctx, grid, ctx->grid[grid], ctx->ld[grid], ctx->tpm, ctx->partials, ctx->partials_len,
-                              out);
+  return launch_tp_any<ArF64>(ctx, grid, A ? static_cast<const double *>(A) : ctx->grid[grid],
+                              static_cast<const double *>(B), sigma, ctx->ld[grid], ctx->tpm, ctx->partials,
+                              ctx->partials_len, out);
 }
 
 int launch_energy_tp_level(hermite_ctx *ctx, int grid, const double *level, int64_t ld, double *partials,
                            int64_t partials_len, double *out) {
   if (!ctx->tpm) return HERMITE_ERR_UNSUPPORTED;
-  return launch_tp_any<ArF64>(ctx, grid, level, ld, ctx->tpm, partials, partials_len, out);
+  return launch_tp_any<ArF64>(ctx, grid, level, nullptr, 0.0f, ld, ctx->tpm, partials, partials_len, out);
 }
 
 }  // namespace hermite

@@ -115,12 +115,17 @@ int launch_half_step_split_into(hermite_ctx *ctx, int dst, const float2 *src, fl
 // Energy reduction (hermite_energy.cu).
 int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const double *B,
                        double *result_slot);
-// Sum-factorised dissipative energies (hermite_energy_tp.cu): both forms of
-// the level held on `grid` into out[0..1]; HERMITE_ERR_UNSUPPORTED when the
-// context has no tensor-product matrices (conservative, or m out of range).
+// Sum-factorised energies (hermite_energy_tp.cu): both forms of the level
+// held on `grid` into out[0..1] (dissipative: plain, invariant; conservative:
+// seminorm, gradient); HERMITE_ERR_UNSUPPORTED when the context has no
+// tensor-product matrices (m out of the compiled range).
 bool energy_tp_supported(int d, int m, int variant);
 int build_energy_tp(hermite_ctx *ctx);
 int launch_energy_tp(hermite_ctx *ctx, int grid, double *out);
+// conservative only: the forms of A + sigma * B (sigma in {0, 1, -1}), A and B
+// levels on `grid` in the context's precision (double or float2 planes,
+// stride ld[grid]); A = NULL means the context's own level
+int launch_energy_tp_pair(hermite_ctx *ctx, int grid, const void *A, const void *B, float sigma, double *out);
 // the same on a caller's FP64 coefficient-major level (plane stride ld) with
 // the given partial-sum scratch (at least 2 x 1184 doubles)
 int launch_energy_tp_level(hermite_ctx *ctx, int grid, const double *level, int64_t ld, double *partials,
