@@ -341,7 +341,9 @@ def run_ours(args):
                          if cpu_v else None),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes + 24},
-        "gpu_launches": (2 * FULL_STEPS_PER_STEP + 4) * args.steps,
+        # per step: one half-step kernel per half-step, then the energy: one
+        # sum-factorised kernel (both forms) and two partial-sum reductions
+        "gpu_launches": (2 * FULL_STEPS_PER_STEP + 3) * args.steps,
         "clocks": split["clocks"],
         "energy_last": [float(x) for x in split["energy"]],
     }
