@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 
+#include "hermite_device.cuh"
 #include "hermite_internal.h"
 
 namespace hermite {
@@ -16,61 +17,16 @@ namespace {
 
 constexpr int kEThreads = 64;
 
+// corners of the cell centred at target node t and its weight in the sum
 template <int D>
 __device__ __forceinline__ void cell_corners_e(const Geometry &g, int64_t t, int64_t *idx, int *gmask,
                                                double *weight) {
-  int64_t ti[D];
-  int64_t r = t;
-#pragma unroll
-  for (int i = D - 1; i >= 0; --i) {
-    ti[i] = r % g.n_dst;
-    r /= g.n_dst;
-  }
-  double w = 1.0;
-  int64_t si[D][2];
-  int gh[D][2];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    // a cell centred on a boundary primal node is cut in half by the boundary
-    if (g.bc != HERMITE_PERIODIC && g.dst == 0 && (ti[i] == 0 || ti[i] == g.n_dst - 1)) w *= 0.5;
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int64_t s = g.dst == 1 ? ti[i] + b : ti[i] - 1 + b;
-      int ghost = 0;
-      if (g.bc == HERMITE_PERIODIC) {
-        if (s < 0) s += g.n_src;
-        if (s >= g.n_src) s -= g.n_src;
-      } else if (s < 0) {
-        s = 0;
-        ghost = 1;
-      } else if (s >= g.n_src) {
-        s = g.n_src - 1;
-        ghost = 1;
-      }
-      si[i][b] = s;
-      gh[i][b] = ghost;
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < (1 << D); ++s) {
-    int64_t id = 0;
-    int mask = 0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const int bit = (s >> (D - 1 - i)) & 1;
-      id = id * g.n_src + si[i][bit];
-      if (gh[i][bit]) mask |= 1 << (D - 1 - i);
-    }
-    idx[s] = id;
-    gmask[s] = mask;
-  }
-  *weight = w;
+  dev::cell_corners<D>(g, t, idx, gmask);
+  *weight = dev::cell_weight<D>(g, t);
 }
 
 __device__ __forceinline__ double gsign(int bc, int mask, int pb) {
-  int neg = __popc(mask & pb) & 1;
-  if (bc == HERMITE_DIRICHLET) neg ^= __popc(mask) & 1;
-  return neg ? -1.0 : 1.0;
+  return dev::ghost_negates(bc, mask, pb) ? -1.0 : 1.0;
 }
 
 // class-c component of the corner Walsh-Hadamard transform of coefficient b

@@ -307,14 +307,7 @@ __global__ void __launch_bounds__(kSFThreads) energy_factored_split_kernel(
       int lg[NC];
       if (t < g.nodes_dst) {
         dev::cell_corners<D>(g, t, li, lg);
-        int64_t r = t;
-        w = 1.0;
-        for (int i = D - 1; i >= 0; --i) {
-          const int64_t ti = r % g.n_dst;
-          r /= g.n_dst;
-          // a cell centred on a boundary primal node is cut in half by the boundary
-          if (g.bc != HERMITE_PERIODIC && g.dst == 0 && (ti == 0 || ti == g.n_dst - 1)) w *= 0.5;
-        }
+        w = dev::cell_weight<D>(g, t);
       } else {
         for (int s = 0; s < NC; ++s) {
           li[s] = 0;

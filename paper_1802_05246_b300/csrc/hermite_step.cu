@@ -9,6 +9,7 @@
 // suffices:  out[a] = sum_b M_0[a][b] z_{par(a) ^ par(b)}[b].
 #include <algorithm>
 
+#include "hermite_device.cuh"
 #include "hermite_internal.h"
 
 namespace hermite {
@@ -16,59 +17,10 @@ namespace {
 
 constexpr int kThreads = 128;
 
-template <int D>
-__device__ __forceinline__ void cell_corners(const Geometry &g, int64_t t, int64_t *idx, int *gmask) {
-  int64_t ti[D];
-  int64_t r = t;
-#pragma unroll
-  for (int i = D - 1; i >= 0; --i) {
-    ti[i] = r % g.n_dst;
-    r /= g.n_dst;
-  }
-  int64_t si[D][2];
-  int gh[D][2];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int64_t s = g.dst == 1 ? ti[i] + b : ti[i] - 1 + b;
-      int ghost = 0;
-      if (g.bc == HERMITE_PERIODIC) {
-        if (s < 0) s += g.n_src;
-        if (s >= g.n_src) s -= g.n_src;
-      } else if (s < 0) {
-        s = 0;
-        ghost = 1;
-      } else if (s >= g.n_src) {
-        s = g.n_src - 1;
-        ghost = 1;
-      }
-      si[i][b] = s;
-      gh[i][b] = ghost;
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < (1 << D); ++s) {
-    int64_t id = 0;
-    int mask = 0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const int bit = (s >> (D - 1 - i)) & 1;
-      id = id * g.n_src + si[i][bit];
-      if (gh[i][bit]) mask |= 1 << (D - 1 - i);
-    }
-    idx[s] = id;
-    gmask[s] = mask;
-  }
-}
-
 // Ghost polynomial sign for a coefficient with parity bits pb when the corner
-// is a ghost in the axes of mask: odd extension (Dirichlet) gives
-// (-1)^{k_i+1} per ghost axis, even extension (Neumann) (-1)^{k_i}.
+// is a ghost in the axes of mask (Sec. 3.1.3).
 __device__ __forceinline__ double ghost_sign(int bc, int mask, int pb) {
-  int neg = __popc(mask & pb) & 1;
-  if (bc == HERMITE_DIRICHLET) neg ^= __popc(mask) & 1;
-  return neg ? -1.0 : 1.0;
+  return dev::ghost_negates(bc, mask, pb) ? -1.0 : 1.0;
 }
 
 template <int D>
@@ -110,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) half_step_f64_kernel(Geometry g, con
   for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < g.nodes_dst; t += stride) {
     int64_t idx[NC];
     int gm[NC];
-    cell_corners<D>(g, t, idx, gm);
+    dev::cell_corners<D>(g, t, idx, gm);
     double acc[CH];
 #pragma unroll
     for (int j = 0; j < CH; ++j) acc[j] = 0.0;
