@@ -122,6 +122,7 @@ int launch_d(hermite_ctx *ctx, const Geometry &g, const double *M, int nci, int 
   if (nco <= 16) return launch_dch<D, 16>(ctx, g, M, nci, nco, src, dst, sub);
   if (nco <= 32) return launch_dch<D, 32>(ctx, g, M, nci, nco, src, dst, sub);
   if (nco <= 64) return launch_dch<D, 64>(ctx, g, M, nci, nco, src, dst, sub);
+  if (nco <= 92) return launch_dch<D, 92>(ctx, g, M, nci, nco, src, dst, sub);  // 3-D m = 3: 91 outputs
   return launch_dch<D, 96>(ctx, g, M, nci, nco, src, dst, sub);
 }
 
