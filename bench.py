@@ -61,7 +61,7 @@ def peaks():
 
 
 FP64_NOMINAL_GFLOPS = 148 * 2 * 2 * 2032e6 / 1e9  # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
-TRAFFIC_PER_LAUNCH = 380.8e6 * 8  # bytes, see profiles/half_step_f64_3d_m3.md
+TRAFFIC_PER_LAUNCH = 373.8e6 * 8  # bytes, see profiles/half_step_f64_3d_m3.md
 SPLIT_TRAFFIC_PER_LAUNCH = 362.3e6 * 8  # bytes, see profiles/half_step_split_3d_m3.md
 FP32_NOMINAL_TOPS = 148 * 128 * 2032e6 / 1e12  # FP32 operations per second, nominal
 SPLIT_OPS_PER_NODE = (NU + NV) * (NU + NV) * 12 + (NU + NV) * D * (1 << D) * 8
@@ -330,7 +330,7 @@ def run_ours(args):
                      # 64^3 (scaled by the node count)
                      "traffic": SPLIT_TRAFFIC_PER_LAUNCH},
         "fp64": {"value": value64, "ms_per_step": fp64["ms"] / args.steps, "dtype": "f64",
-                 "roofline": {"bound": "alu", "kernel": "half_step_f64_kernel<3,96>", "achieved": achieved64,
+                 "roofline": {"bound": "alu", "kernel": "half_step_f64_kernel<3,92>", "achieved": achieved64,
                               "peak": FP64_NOMINAL_GFLOPS / 1e3, "unit": "TFLOP/s",
                               "frac": achieved64 / (FP64_NOMINAL_GFLOPS / 1e3), "launch_ms": fp64["half_ms"],
                               "traffic": TRAFFIC_PER_LAUNCH},
