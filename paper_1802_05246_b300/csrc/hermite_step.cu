@@ -128,32 +128,44 @@ int launch_d(hermite_ctx *ctx, const Geometry &g, const double *M, int nci, int 
 
 // host layout [node][coef] (u block then v block) <-> SoA planes [coef][ld]
 // (values copied unchanged: the device holds the paper's scaled data).
+// Layout conversions through a shared-memory tile of 32 nodes x all
+// coefficients: the node-major side is read or written as one contiguous run
+// per tile, the coefficient-major side as 32-node runs per plane.
+constexpr int kTileNodes = 32;
+
 __global__ void to_soa_kernel(const double *__restrict__ hu, const double *__restrict__ hv, int64_t nodes,
                               int nu, int nv, double vscale, double *__restrict__ soa, int64_t ld) {
-  const int64_t total = nodes * (nu + nv);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = i / nodes, node = i % nodes;
-    double v;
-    if (k < nu)
-      v = hu[node * nu + k];
-    else
-      v = hv ? vscale * hv[node * nv + (k - nu)] : 0.0;
-    soa[k * ld + node] = v;
+  extern __shared__ double tile[];  // [kTileNodes][nu + nv + 1]
+  const int nc = nu + nv, pitch = nc + 1;
+  for (int64_t n0 = (int64_t)blockIdx.x * kTileNodes; n0 < nodes; n0 += (int64_t)gridDim.x * kTileNodes) {
+    const int cnt = (int)(nodes - n0 < kTileNodes ? nodes - n0 : kTileNodes);
+    for (int e = threadIdx.x; e < cnt * nu; e += blockDim.x) tile[(e / nu) * pitch + e % nu] = hu[n0 * nu + e];
+    for (int e = threadIdx.x; e < cnt * nv; e += blockDim.x)
+      tile[(e / nv) * pitch + nu + e % nv] = hv ? vscale * hv[n0 * nv + e] : 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * kTileNodes; e += blockDim.x) {
+      const int k = e / kTileNodes, r = e % kTileNodes;
+      if (r < cnt) soa[(int64_t)k * ld + n0 + r] = tile[r * pitch + k];
+    }
+    __syncthreads();
   }
 }
 
 __global__ void from_soa_kernel(const double *__restrict__ soa, int64_t ld, int64_t nodes, int nu, int nv,
                                 double vscale, double *__restrict__ hu, double *__restrict__ hv) {
-  const int64_t total = nodes * (nu + nv);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t node = i / (nu + nv), k = i % (nu + nv);
-    const double v = soa[k * ld + node];
-    if (k < nu)
-      hu[node * nu + k] = v;
-    else
-      hv[node * nv + (k - nu)] = vscale * v;
+  extern __shared__ double tile[];  // [kTileNodes][nu + nv + 1]
+  const int nc = nu + nv, pitch = nc + 1;
+  for (int64_t n0 = (int64_t)blockIdx.x * kTileNodes; n0 < nodes; n0 += (int64_t)gridDim.x * kTileNodes) {
+    const int cnt = (int)(nodes - n0 < kTileNodes ? nodes - n0 : kTileNodes);
+    for (int e = threadIdx.x; e < nc * kTileNodes; e += blockDim.x) {
+      const int k = e / kTileNodes, r = e % kTileNodes;
+      if (r < cnt) tile[r * pitch + k] = soa[(int64_t)k * ld + n0 + r];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * nu; e += blockDim.x) hu[n0 * nu + e] = tile[(e / nu) * pitch + e % nu];
+    for (int e = threadIdx.x; e < cnt * nv; e += blockDim.x)
+      hv[n0 * nv + e] = vscale * tile[(e / nv) * pitch + nu + e % nv];
+    __syncthreads();
   }
 }
 
@@ -189,8 +201,9 @@ int launch_to_device_layout(hermite_ctx *ctx, const double *hu, const double *hv
   const int nv = has_v ? ctx->Nv : 0;
   const int64_t total = nodes * (nu_count + nv);
   if (total == 0) return HERMITE_OK;
-  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
-  to_soa_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(hu, hv, nodes, nu_count, nv, 1.0, soa, ld);
+  const int64_t blocks = std::min<int64_t>((nodes + kTileNodes - 1) / kTileNodes, 148 * 16);
+  const size_t smem = sizeof(double) * kTileNodes * (nu_count + nv + 1);
+  to_soa_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(hu, hv, nodes, nu_count, nv, 1.0, soa, ld);
   return cuda_ok(ctx, cudaGetLastError(), "to_soa_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
@@ -199,8 +212,9 @@ int launch_to_host_layout(hermite_ctx *ctx, const double *soa, int64_t ld, int64
   const int nv = want_v ? ctx->Nv : 0;
   const int64_t total = nodes * (ctx->Nu + nv);
   if (total == 0) return HERMITE_OK;
-  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
-  from_soa_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(soa, ld, nodes, ctx->Nu, nv, 1.0, hu, hv);
+  const int64_t blocks = std::min<int64_t>((nodes + kTileNodes - 1) / kTileNodes, 148 * 16);
+  const size_t smem = sizeof(double) * kTileNodes * (ctx->Nu + nv + 1);
+  from_soa_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(soa, ld, nodes, ctx->Nu, nv, 1.0, hu, hv);
   return cuda_ok(ctx, cudaGetLastError(), "from_soa_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
