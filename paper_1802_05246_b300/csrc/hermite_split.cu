@@ -453,24 +453,25 @@ __global__ void split_operator_kernel(const double *M, int nci, const int16_t *o
   }
 }
 
+// plane-wise conversions (grid.y = coefficient plane, no division per element)
 __global__ void to_split_kernel(const double *__restrict__ a, int64_t ld, int planes, int64_t nodes,
                                 float2 *__restrict__ out) {
-  const int64_t total = (int64_t)planes * ld;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i % ld >= nodes) continue;
-    const double x = a[i];
+  const double *src = a + (int64_t)blockIdx.y * ld;
+  float2 *dst = out + (int64_t)blockIdx.y * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = src[i];
     const float hi = __double2float_rn(x);
-    out[i] = make_float2(hi, __double2float_rn(x - (double)hi));
+    dst[i] = make_float2(hi, __double2float_rn(x - (double)hi));
   }
 }
 
 __global__ void from_split_kernel(const float2 *__restrict__ a, int64_t ld, int planes, int64_t nodes,
                                   double *__restrict__ out) {
-  const int64_t total = (int64_t)planes * ld;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i % ld >= nodes) continue;
-    const float2 v = a[i];
-    out[i] = (double)v.x + (double)v.y;
+  const float2 *src = a + (int64_t)blockIdx.y * ld;
+  double *dst = out + (int64_t)blockIdx.y * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = src[i];
+    dst[i] = (double)v.x + (double)v.y;
   }
 }
 
@@ -651,19 +652,24 @@ int launch_half_step_split(hermite_ctx *ctx, int dst, bool subtract_old) {
   return HERMITE_ERR_ARG;
 }
 
+// blocks per plane: about 8 waves of 256-thread blocks over the whole grid
+static dim3 plane_grid(const hermite_ctx *ctx, int grid) {
+  const int64_t per_plane = std::max<int64_t>(1, std::min<int64_t>((ctx->nodes[grid] + 255) / 256,
+                                                                    (148 * 64 + ctx->ncoef - 1) / ctx->ncoef));
+  return dim3((unsigned)per_plane, (unsigned)ctx->ncoef);
+}
+
 int split_from_fp64(hermite_ctx *ctx, int grid) {
-  const int64_t total = (int64_t)ctx->ncoef * ctx->ld[grid];
-  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
-  to_split_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, ctx->stream>>>(
-      ctx->grid[grid], ctx->ld[grid], ctx->ncoef, ctx->nodes[grid], ctx->fgrid[grid]);
+  if (ctx->nodes[grid] == 0) return HERMITE_OK;
+  to_split_kernel<<<plane_grid(ctx, grid), 256, 0, ctx->stream>>>(ctx->grid[grid], ctx->ld[grid], ctx->ncoef,
+                                                                  ctx->nodes[grid], ctx->fgrid[grid]);
   return cuda_ok(ctx, cudaGetLastError(), "to_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
 int split_to_fp64(hermite_ctx *ctx, int grid) {
-  const int64_t total = (int64_t)ctx->ncoef * ctx->ld[grid];
-  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
-  from_split_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, ctx->stream>>>(
-      ctx->fgrid[grid], ctx->ld[grid], ctx->ncoef, ctx->nodes[grid], ctx->grid[grid]);
+  if (ctx->nodes[grid] == 0) return HERMITE_OK;
+  from_split_kernel<<<plane_grid(ctx, grid), 256, 0, ctx->stream>>>(ctx->fgrid[grid], ctx->ld[grid], ctx->ncoef,
+                                                                    ctx->nodes[grid], ctx->grid[grid]);
   return cuda_ok(ctx, cudaGetLastError(), "from_split_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
