@@ -76,12 +76,9 @@ void release(hermite_ctx *ctx) {
   cudaFree(ctx->partials);
   cudaFree(ctx->result);
   for (int g = 0; g < 2; ++g) cudaFree(ctx->fgrid[g]);
-  cudaFree(ctx->Mc);
   cudaFree(ctx->fscratch);
-  cudaFree(ctx->outrow);
-  cudaFree(ctx->npc);
-  if (ctx->Mp != ctx->Mc) cudaFree(ctx->Mp);
-  if (ctx->prow != ctx->outrow) cudaFree(ctx->prow);
+  cudaFree(ctx->Mp);
+  cudaFree(ctx->prow);
   cudaFree(ctx->pcls);
   cudaFree(ctx->tpm);
   cudaFree(ctx->tpmf);

@@ -67,15 +67,12 @@ struct hermite_ctx {
   int precision = 0;
   bool has_energy = true;      // energy forms built (batch problems skip them)
   float2 *fgrid[2] = {nullptr, nullptr};  // SoA [ncoef][ld] of (hi, lo)
-  float2 *Mc = nullptr;        // operator rows grouped by output parity class
   float2 *Lf[hermite::kNumForms] = {nullptr, nullptr};  // energy factors split hi + lo
   float2 *fscratch = nullptr;  // one split grid (conservative energy)
-  int16_t *outrow = nullptr;   // [2^d][nomax] output row of each class slot (-1 unused)
-  int8_t *npc = nullptr;       // outputs per class
-  int nomax = 0;
-  // slot packing of the single-problem split half-step: warp w's slots
-  // [0, psplit) hold outputs of parity class pcls[2w], slots [psplit, pslots)
-  // outputs of class pcls[2w+1]; the operator is laid out per warp
+  // slot layout of the split half-step kernels (single problem and batch):
+  // warp w's slots [0, psplit) hold outputs of parity class pcls[2w], slots
+  // [psplit, pslots) outputs of class pcls[2w+1]; the operator is laid out
+  // per warp
   float2 *Mp = nullptr;        // [2^d warp][nci][pslots]
   int16_t *prow = nullptr;     // [2^d][pslots] output row of each slot (-1 unused)
   int8_t *pcls = nullptr;      // [2^d][2]

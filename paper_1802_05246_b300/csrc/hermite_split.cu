@@ -436,15 +436,15 @@ int launch_energy_split_d(hermite_ctx *ctx, int form, int grid, const float2 *A,
 
 // operator rows in a warp slot layout, each entry split hi + lo; the entries
 // of slots 2k and 2k+1 for one input are stored (hi, hi, lo, lo)
-__global__ void split_operator_kernel(const double *M, int nci, const int16_t *outrow, int nclass, int nomax,
-                                      float2 *Mc) {
-  const int64_t n = (int64_t)nclass * nci * nomax;
-  float *f = reinterpret_cast<float *>(Mc);
+__global__ void split_operator_kernel(const double *M, int nci, const int16_t *prow, int nwarps, int S,
+                                      float2 *Mp) {
+  const int64_t n = (int64_t)nwarps * nci * S;
+  float *f = reinterpret_cast<float *>(Mp);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(i % nomax);
-    const int b = (int)((i / nomax) % nci);
-    const int c = (int)(i / ((int64_t)nomax * nci));
-    const int row = outrow[c * nomax + j];
+    const int j = (int)(i % S);
+    const int b = (int)((i / S) % nci);
+    const int w = (int)(i / ((int64_t)S * nci));
+    const int row = prow[w * S + j];
     const double m = row >= 0 ? M[(size_t)row * nci + b] : 0.0;
     const float hi = __double2float_rn(m);
     const int64_t base = 2 * (i - j) + 4 * (j / 2) + (j & 1);
@@ -521,90 +521,63 @@ bool pack_two_classes(const std::vector<int> &counts, int S, int P, std::vector<
 
 int build_split_operator(hermite_ctx *ctx) {
   const int nclass = 1 << ctx->d;
-  // group output rows by parity class
-  std::vector<int> counts(nclass, 0);
+  // output rows by parity class
   std::vector<int8_t> parh(ctx->Nu + ctx->Nv);
   if (!cuda_ok(ctx, cudaMemcpy(parh.data(), ctx->par_in, parh.size(), cudaMemcpyDeviceToHost), "parity copy"))
     return HERMITE_ERR_CUDA;
-  for (int r = 0; r < ctx->nco; ++r) counts[parh[r]]++;
-  int nomax = 0;
-  for (int c = 0; c < nclass; ++c) nomax = std::max(nomax, counts[c]);
-  // slots per class warp: the smallest even count that holds the largest class
-  // (up to 16; then 24 or 32)
-  ctx->nomax = nomax <= 16 ? std::max(2, (nomax + 1) / 2 * 2) : (nomax <= 24 ? 24 : 32);
-  if (nomax > 32) return HERMITE_ERR_UNSUPPORTED;
-  std::vector<int16_t> outrow((size_t)nclass * ctx->nomax, -1);
-  std::vector<int8_t> npc(nclass, 0);
-  for (int r = 0; r < ctx->nco; ++r) {
-    const int c = parh[r];
-    outrow[(size_t)c * ctx->nomax + npc[c]] = (int16_t)r;
-    npc[c]++;
-  }
-  if (!cuda_ok(ctx, device_alloc(&ctx->outrow, sizeof(int16_t) * outrow.size()), "cudaMalloc outrow") ||
-      !cuda_ok(ctx, device_alloc(&ctx->npc, nclass), "cudaMalloc npc") ||
-      !cuda_ok(ctx, device_alloc(&ctx->Mc, sizeof(float2) * (size_t)nclass * ctx->nci * ctx->nomax), "cudaMalloc Mc") ||
-      !cuda_ok(ctx, device_alloc(&ctx->pcls, 2 * nclass), "cudaMalloc pcls"))
-    return HERMITE_ERR_ALLOC;
-  if (!cuda_ok(ctx, cudaMemcpy(ctx->outrow, outrow.data(), sizeof(int16_t) * outrow.size(), cudaMemcpyHostToDevice),
-               "outrow copy") ||
-      !cuda_ok(ctx, cudaMemcpy(ctx->npc, npc.data(), nclass, cudaMemcpyHostToDevice), "npc copy"))
-    return HERMITE_ERR_CUDA;
-  split_operator_kernel<<<64, 256, 0, ctx->stream>>>(ctx->M, ctx->nci, ctx->outrow, nclass, ctx->nomax, ctx->Mc);
-  if (!cuda_ok(ctx, cudaGetLastError(), "split_operator_kernel")) return HERMITE_ERR_CUDA;
-
-  // the single-problem kernel: two classes per warp where that needs fewer
-  // slots, else the class layout above
   std::vector<std::vector<int>> rows(nclass);
   for (int r = 0; r < ctx->nco; ++r) rows[parh[r]].push_back(r);
-  std::vector<int> bins;
-  int S = ctx->nomax, P = ctx->nomax;
+  std::vector<int> counts(nclass);
+  for (int c = 0; c < nclass; ++c) counts[c] = (int)rows[c].size();
   const int cmax = *std::max_element(counts.begin(), counts.end());
-  for (int cand = 2; cand < ctx->nomax && S == ctx->nomax; cand += 2) {
+  if (cmax > 32) return HERMITE_ERR_UNSUPPORTED;
+  // one class per warp: the smallest even slot count that holds the largest
+  // class (up to 16; then 24 or 32) ...
+  const int one = cmax <= 16 ? std::max(2, (cmax + 1) / 2 * 2) : (cmax <= 24 ? 24 : 32);
+  std::vector<int> bins(2 * nclass, -1);  // class of warp w's first P / last S - P slots
+  for (int w = 0; w < nclass; ++w) bins[w] = w;
+  int S = one, P = one;
+  // ... unless a layout with fewer slots holds the classes, two per warp
+  for (int cand = 2; cand < one && S == one; cand += 2) {
     if (cmax <= cand && std::find(std::begin(kOneClassLayouts), std::end(kOneClassLayouts), cand) !=
                             std::end(kOneClassLayouts)) {
-      bins.assign(2 * nclass, -1);
-      for (int w = 0; w < nclass; ++w) bins[w] = w;
       S = P = cand;
     } else if (nclass > 1) {
+      std::vector<int> packed;
       for (const auto &l : kTwoClassLayouts)
-        if (l[0] == cand && pack_two_classes(counts, l[0], l[1], &bins)) {
+        if (l[0] == cand && pack_two_classes(counts, l[0], l[1], &packed)) {
           S = l[0];
           P = l[1];
+          bins = packed;
           break;
         }
     }
   }
   std::vector<int8_t> cls(2 * nclass);
-  if (S == ctx->nomax) {
-    for (int w = 0; w < nclass; ++w) cls[2 * w] = cls[2 * w + 1] = (int8_t)w;
-    ctx->Mp = ctx->Mc;
-    ctx->prow = ctx->outrow;
-  } else {
-    // bins[w] / bins[nclass + w]: class of warp w's first P / last S - P slots
-    std::vector<int16_t> prow((size_t)nclass * S, -1);
-    std::vector<size_t> next(nclass, 0);
-    for (int part = 0; part < 2; ++part)
-      for (int w = 0; w < nclass; ++w) {
-        const int c = bins[part * nclass + w];
-        const int j0 = part ? P : 0, j1 = part ? S : P;
-        cls[2 * w + part] = (int8_t)(c < 0 ? (part ? cls[2 * w] : 0) : c);
-        for (int j = j0; j < j1 && c >= 0 && next[c] < rows[c].size(); ++j)
-          prow[(size_t)w * S + j] = (int16_t)rows[c][next[c]++];
-      }
-    for (int c = 0; c < nclass; ++c)
-      if (next[c] != rows[c].size()) return HERMITE_ERR_UNSUPPORTED;  // not reached: the packing covers every row
-    if (!cuda_ok(ctx, device_alloc(&ctx->prow, sizeof(int16_t) * prow.size()), "cudaMalloc prow") ||
-        !cuda_ok(ctx, device_alloc(&ctx->Mp, sizeof(float2) * (size_t)nclass * ctx->nci * S), "cudaMalloc Mp"))
-      return HERMITE_ERR_ALLOC;
-    if (!cuda_ok(ctx, cudaMemcpy(ctx->prow, prow.data(), sizeof(int16_t) * prow.size(), cudaMemcpyHostToDevice),
-                 "prow copy"))
-      return HERMITE_ERR_CUDA;
-    split_operator_kernel<<<64, 256, 0, ctx->stream>>>(ctx->M, ctx->nci, ctx->prow, nclass, S, ctx->Mp);
-  }
+  std::vector<int16_t> prow((size_t)nclass * S, -1);
+  std::vector<size_t> next(nclass, 0);
+  for (int part = 0; part < 2; ++part)
+    for (int w = 0; w < nclass; ++w) {
+      const int c = bins[part * nclass + w];
+      const int j0 = part ? P : 0, j1 = part ? S : P;
+      cls[2 * w + part] = (int8_t)(c < 0 ? (part ? cls[2 * w] : 0) : c);
+      for (int j = j0; j < j1 && c >= 0 && next[c] < rows[c].size(); ++j)
+        prow[(size_t)w * S + j] = (int16_t)rows[c][next[c]++];
+    }
+  for (int c = 0; c < nclass; ++c)
+    if (next[c] != rows[c].size()) return HERMITE_ERR_UNSUPPORTED;  // not reached: the layout holds every row
+  if (!cuda_ok(ctx, device_alloc(&ctx->prow, sizeof(int16_t) * prow.size()), "cudaMalloc prow") ||
+      !cuda_ok(ctx, device_alloc(&ctx->pcls, 2 * nclass), "cudaMalloc pcls") ||
+      !cuda_ok(ctx, device_alloc(&ctx->Mp, sizeof(float2) * (size_t)nclass * ctx->nci * S), "cudaMalloc Mp"))
+    return HERMITE_ERR_ALLOC;
+  if (!cuda_ok(ctx, cudaMemcpy(ctx->prow, prow.data(), sizeof(int16_t) * prow.size(), cudaMemcpyHostToDevice),
+               "prow copy") ||
+      !cuda_ok(ctx, cudaMemcpy(ctx->pcls, cls.data(), cls.size(), cudaMemcpyHostToDevice), "pcls copy"))
+    return HERMITE_ERR_CUDA;
+  split_operator_kernel<<<64, 256, 0, ctx->stream>>>(ctx->M, ctx->nci, ctx->prow, nclass, S, ctx->Mp);
   ctx->pslots = S;
   ctx->psplit = P;
-  if (!cuda_ok(ctx, cudaMemcpy(ctx->pcls, cls.data(), cls.size(), cudaMemcpyHostToDevice), "pcls copy") ||
-      !cuda_ok(ctx, cudaGetLastError(), "split_operator_kernel") ||
+  if (!cuda_ok(ctx, cudaGetLastError(), "split_operator_kernel") ||
       !cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "split operator sync"))
     return HERMITE_ERR_CUDA;
   return HERMITE_OK;
