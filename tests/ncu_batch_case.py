@@ -1,7 +1,9 @@
 """Small case for an ncu capture of the ragged-batch split kernel (not a test):
 the first 128 problems of the seed-0 ragged 2-D workload (N in
 {32,64,128,256}^2, m in 2..6, mixed boundaries), dissipative, split precision,
-two full steps on a non-default stream.  Usage: python tests/ncu_batch_case.py"""
+two full steps on a non-default stream, with the item size and blocks per SM
+the autotuner picks on the full workload (256 nodes, 8 blocks per SM).
+Usage: python tests/ncu_batch_case.py"""
 import os
 import sys
 
@@ -22,6 +24,7 @@ for _ in range(128):
     probs.append((2, m, Np, 1.0, 1.0 / Np, 0.9 / Np, hb.DISSIPATIVE, bc))
 b = hb.HermiteBatch(probs, precision=hb.SPLIT32)
 b.set_stream(torch.cuda.Stream())
+b.config(256, 8)
 b.step(2)
 torch.cuda.synchronize()
 print("ok", b.dof_per_step)
