@@ -109,13 +109,31 @@ __global__ void __launch_bounds__(kBT) batch_f64_kernel(const BatchDesc *__restr
 // one item = a range of target nodes processed 32 at a time by 2^d warps;
 // warp w accumulates NS output slots, the first NP of parity class pcls[2w]
 // and the rest of class pcls[2w+1] (the contexts' slot layout)
+// 16-byte asynchronous copy global -> shared (completion tracked in groups)
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Shared memory of the split batch kernel: the operator rows of the current
+// and the next chunk per warp (copied one chunk ahead), then the exchange
+// buffer of the transformed corner data.
+template <int D, int NS>
+constexpr size_t batch_split_smem() {
+  return sizeof(float2) * (2 * (1 << D) * (1 << D) * NS + (1 << D) * (1 << D) * 32);
+}
+
 template <int D, int NS, int NP>
 __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *__restrict__ descs,
                                                               const BatchItem *__restrict__ items, int nitems,
                                                               unsigned *counter) {
   static_assert(NS % 2 == 0 && NP % 2 == 0, "slot pairs never straddle the two classes");
   constexpr int NC = 1 << D;
-  __shared__ float2 Y[NC * NC * 32];
+  extern __shared__ __align__(16) float2 bsm[];
+  float2 *Ms = bsm;                     // [2 buffers][NC warps][NC rows][NS]
+  float2 *Y = Ms + 2 * NC * NC * NS;    // [NC][NC][32]
   __shared__ int item_s;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (;;) {
@@ -147,7 +165,19 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
       float2 ahi[NS / 2], alo[NS / 2];
 #pragma unroll
       for (int k = 0; k < NS / 2; ++k) ahi[k] = alo[k] = make_float2(0.f, 0.f);
-      for (int b0 = 0; b0 < P.nci; b0 += NC) {
+      // this warp's operator rows b0 .. b0+NC-1 (contiguous) into buffer buf
+      auto stage = [&](int b0, int buf) {
+        const int kc = min(NC, P.nci - b0);
+        const float2 *g = P.Mp + ((size_t)w * P.nci + b0) * NS;
+        float2 *sdst = Ms + ((size_t)buf * NC + w) * NC * NS;
+        for (int e = lane; e < kc * NS / 2; e += 32) cp_async16(sdst + 2 * e, g + 2 * e);
+      };
+      stage(0, 0);
+      cp_async_commit();
+      for (int b0 = 0, ch = 0; b0 < P.nci; b0 += NC, ++ch) {
+        // the next chunk's rows are in flight while this one is used
+        if (b0 + NC < P.nci) stage(b0 + NC, (ch + 1) & 1);
+        cp_async_commit();
         const int b = b0 + w;
         if (b < P.nci) {
           const float2 *plane = src + (size_t)b * P.g.ld_src;
@@ -172,6 +202,9 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
           for (int q = 0; q < NC; ++q) Y[(w * NC + q) * 32 + lane] = x[q];
         }
         __syncthreads();
+        cp_async_wait_prev();  // this chunk's rows have landed (each warp reads its own)
+        __syncwarp();
+        const float2 *mbuf = Ms + ((size_t)(ch & 1) * NC + w) * NC * NS;
         const int kmax = min(NC, P.nci - b0);
         for (int k = 0; k < kmax; ++k) {
           const int bb = b0 + k;
@@ -180,16 +213,13 @@ __global__ void __launch_bounds__(32 << D) batch_split_kernel(const BatchDesc *_
           const float2 yb = NP < NS ? Y[(k * NC + (cB ^ pb)) * 32 + lane] : ya;
           const float2 yah = make_float2(ya.x, ya.x), yal = make_float2(ya.y, ya.y), yan = make_float2(-ya.x, -ya.x);
           const float2 ybh = make_float2(yb.x, yb.x), ybl = make_float2(yb.y, yb.y), ybn = make_float2(-yb.x, -yb.x);
-          const float4 *mrow = reinterpret_cast<const float4 *>(P.Mp + ((size_t)w * P.nci + bb) * NS);
+          const float4 *mrow = reinterpret_cast<const float4 *>(mbuf + k * NS);
 #pragma unroll
           for (int j = 0; j < NS / 2; ++j) {
-            const float4 mm = __ldg(mrow + j);  // (hi, hi, lo, lo) of slots 2j, 2j+1
-            if constexpr (NS >= 24 || NS == 2) {
-              // measured: with 24 or more slots the packed pairs ran far slower
-              // in this kernel (operator rows from global memory) than the
-              // scalar form, and with one slot pair forming the packed copies
-              // of y costs what the packing saves; these layouts keep the
-              // scalar form
+            const float4 mm = mrow[j];  // (hi, hi, lo, lo) of slots 2j, 2j+1
+            if constexpr (NS == 2) {
+              // one slot pair: forming the packed copies of y costs what the
+              // packing saves (measured), so the scalar form
               float2 a0 = make_float2(ahi[j].x, alo[j].x), a1 = make_float2(ahi[j].y, alo[j].y);
               dev::df_fma(a0, make_float2(mm.x, mm.z), 2 * j < NP ? ya : yb);
               dev::df_fma(a1, make_float2(mm.y, mm.w), 2 * j < NP ? ya : yb);
@@ -364,8 +394,14 @@ int launch_group(hermite_batch *b, int k, const hermite_batch::Group &gr, unsign
     // the template must equal the contexts' slot layout: it is the stride of their split operators
 #define HERMITE_BATCH_LAYOUT(S_, P_)                                                                          \
   if (gr.tmpl == S_ * 64 + P_) {                                                                              \
-    batch_split_kernel<D, S_, P_><<<blocks, 32 << D, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems,     \
-                                                                     counter);                                \
+    constexpr size_t smem = batch_split_smem<D, S_>();                                                        \
+    if (smem > 48 * 1024 &&                                                                                   \
+        !bok(b, cudaFuncSetAttribute(batch_split_kernel<D, S_, P_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)smem),                                                              \
+             "batch kernel shared memory"))                                                                   \
+      return HERMITE_ERR_CUDA;                                                                                \
+    batch_split_kernel<D, S_, P_><<<blocks, 32 << D, smem, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems,  \
+                                                                        counter);                             \
     return bok(b, cudaGetLastError(), "batch kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;                      \
   }
     HERMITE_BATCH_LAYOUT(2, 2)
