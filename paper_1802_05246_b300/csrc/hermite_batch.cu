@@ -395,7 +395,7 @@ int launch_group(hermite_batch *b, int k, const hermite_batch::Group &gr, unsign
 #define HERMITE_BATCH_LAYOUT(S_, P_)                                                                          \
   if (gr.tmpl == S_ * 64 + P_) {                                                                              \
     constexpr size_t smem = batch_split_smem<D, S_>();                                                        \
-    if (smem > 48 * 1024 &&                                                                                   \
+    if (smem > 40 * 1024 && /* the block also holds a little static shared memory */                        \
         !bok(b, cudaFuncSetAttribute(batch_split_kernel<D, S_, P_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      (int)smem),                                                              \
              "batch kernel shared memory"))                                                                   \
