@@ -37,71 +37,83 @@ struct BatchDesc {
 // ---------------------------------------------------------------- FP64
 constexpr int kBT = 128;
 
+// One item = a node range of one problem; the block first copies that
+// problem's operator (all nco <= CH outputs, transposed to [input][output])
+// into shared memory, then each thread takes nodes: corner gather, transform,
+// and every output from the staged rows in one pass.
 template <int D, int CH>
 __global__ void __launch_bounds__(kBT) batch_f64_kernel(const BatchDesc *__restrict__ descs,
                                                         const BatchItem *__restrict__ items, int nitems,
                                                         unsigned *counter) {
   constexpr int NC = 1 << D;
-  __shared__ double zb[NC * kBT];
+  extern __shared__ __align__(16) double fsm[];
+  double *Ms = fsm;              // [nci][CH]
+  double *zb = Ms + CH * CH;     // [NC][kBT]  (nci <= nco <= CH)
   __shared__ int item_s;
+  __shared__ int staged;         // problem whose operator Ms holds (-1: none)
   double *myz = zb + threadIdx.x;
+  if (threadIdx.x == 0) staged = -1;
   for (;;) {
     if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
     __syncthreads();
     const int it = item_s;
-    __syncthreads();
     if (it >= nitems) break;
     const BatchItem I = items[it];
     const BatchDesc P = descs[I.prob];
+    if (staged != I.prob) {  // uniform: every thread read the same item
+      for (int e = threadIdx.x; e < P.nci * CH; e += kBT) {
+        const int bb = e / CH, j = e % CH;
+        Ms[e] = j < P.nco ? P.M[(size_t)j * P.nci + bb] : 0.0;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) staged = I.prob;
+    }
     const double *src = static_cast<const double *>(P.src);
     double *dst = static_cast<double *>(P.dst);
+    int po[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) po[j] = j < P.nco ? P.par[j] : 0;
     for (int64_t t = I.n0 + threadIdx.x; t < I.n1; t += kBT) {
       int64_t idx[NC];
       int gm[NC];
       dev::cell_corners<D>(P.g, t, idx, gm);
-      for (int c0 = 0; c0 < P.nco; c0 += CH) {
-        double acc[CH];
-        int po[CH];
+      double acc[CH];
 #pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          acc[j] = 0.0;
-          po[j] = (c0 + j < P.nco) ? P.par[c0 + j] : 0;
-        }
-        for (int b = 0; b < P.nci; ++b) {
-          const double *plane = src + (size_t)b * P.g.ld_src;
-          const int pb = P.par[b];
-          double x[NC];
+      for (int j = 0; j < CH; ++j) acc[j] = 0.0;
+      for (int b = 0; b < P.nci; ++b) {
+        const double *plane = src + (size_t)b * P.g.ld_src;
+        const int pb = P.par[b];
+        double x[NC];
 #pragma unroll
-          for (int s = 0; s < NC; ++s) {
-            double v = __ldg(plane + idx[s]);
-            if (gm[s] && dev::ghost_negates(P.g.bc, gm[s], pb)) v = -v;
-            x[s] = v;
-          }
-#pragma unroll
-          for (int bm = 1; bm < NC; bm <<= 1)
-#pragma unroll
-            for (int i = 0; i < NC; ++i)
-              if (!(i & bm)) {
-                const double a = x[i], c = x[i | bm];
-                x[i] = a + c;
-                x[i | bm] = a - c;
-              }
-#pragma unroll
-          for (int s = 0; s < NC; ++s) myz[s * kBT] = x[s];
-#pragma unroll
-          for (int j = 0; j < CH; ++j)
-            if (c0 + j < P.nco)
-              acc[j] = fma(__ldg(P.M + (size_t)(c0 + j) * P.nci + b), myz[(po[j] ^ pb) * kBT], acc[j]);
+        for (int s = 0; s < NC; ++s) {
+          double v = __ldg(plane + idx[s]);
+          if (gm[s] && dev::ghost_negates(P.g.bc, gm[s], pb)) v = -v;
+          x[s] = v;
         }
 #pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          if (c0 + j < P.nco) {
-            double *o = dst + (size_t)(c0 + j) * P.g.ld_dst + t;
-            *o = P.sub ? acc[j] - *o : acc[j];
-          }
+        for (int bm = 1; bm < NC; bm <<= 1)
+#pragma unroll
+          for (int i = 0; i < NC; ++i)
+            if (!(i & bm)) {
+              const double a = x[i], c = x[i | bm];
+              x[i] = a + c;
+              x[i | bm] = a - c;
+            }
+#pragma unroll
+        for (int s = 0; s < NC; ++s) myz[s * kBT] = x[s];
+        const double *mrow = Ms + (size_t)b * CH;
+#pragma unroll
+        for (int j = 0; j < CH; ++j) acc[j] = fma(mrow[j], myz[(po[j] ^ pb) * kBT], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        if (j < P.nco) {
+          double *o = dst + (size_t)j * P.g.ld_dst + t;
+          *o = P.sub ? acc[j] - *o : acc[j];
         }
       }
     }
+    __syncthreads();  // item_s and the staged rows are rewritten next
   }
 }
 
@@ -303,7 +315,8 @@ void free_items(hermite_batch *b) {
 
 int group_key(const hermite_batch *b, const hermite_ctx *ctx) {
   if (b->precision == HERMITE_SPLIT32) return ctx->pslots * 64 + ctx->psplit;
-  return ctx->nco <= 8 ? 8 : (ctx->nco <= 16 ? 16 : (ctx->nco <= 32 ? 32 : 48));
+  // FP64: the output count rounded up to a compiled chunk (all outputs in one)
+  return ctx->nco <= 8 ? 8 : (ctx->nco <= 16 ? 16 : (ctx->nco <= 32 ? 32 : (ctx->nco <= 48 ? 48 : 96)));
 }
 
 int build_items(hermite_batch *b) {
@@ -432,12 +445,24 @@ int launch_group(hermite_batch *b, int k, const hermite_batch::Group &gr, unsign
 #undef HERMITE_BATCH_LAYOUT
     return HERMITE_ERR_ARG;
   } else {
-    switch (gr.tmpl) {
-      case 8: batch_f64_kernel<D, 8><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 16: batch_f64_kernel<D, 16><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      case 32: batch_f64_kernel<D, 32><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-      default: batch_f64_kernel<D, 48><<<blocks, kBT, 0, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); break;
-    }
+#define HERMITE_BATCH_F64(CH_)                                                                              \
+  if (gr.tmpl == CH_) {                                                                                     \
+    const size_t smem = sizeof(double) * ((size_t)CH_ * CH_ + (1 << D) * kBT);                              \
+    if (smem > 40 * 1024 &&                                                                                 \
+        !bok(b, cudaFuncSetAttribute(batch_f64_kernel<D, CH_>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                     (int)smem),                                                            \
+             "batch kernel shared memory"))                                                                 \
+      return HERMITE_ERR_CUDA;                                                                              \
+    batch_f64_kernel<D, CH_><<<blocks, kBT, smem, b->stream>>>(b->d_desc[k], gr.d_items, gr.nitems, counter); \
+    return bok(b, cudaGetLastError(), "batch kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;                    \
+  }
+    HERMITE_BATCH_F64(8)
+    HERMITE_BATCH_F64(16)
+    HERMITE_BATCH_F64(32)
+    HERMITE_BATCH_F64(48)
+    HERMITE_BATCH_F64(96)
+#undef HERMITE_BATCH_F64
+    return HERMITE_ERR_ARG;
   }
   return bok(b, cudaGetLastError(), "batch kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
