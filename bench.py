@@ -60,10 +60,16 @@ def peaks():
         return {}
 
 
-FP64_NOMINAL_GFLOPS = 148 * 2 * 2 * 2032e6 / 1e9  # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
-TRAFFIC_PER_LAUNCH = 373.8e6 * 8  # bytes, see profiles/half_step_f64_3d_m3.md
-SPLIT_TRAFFIC_PER_LAUNCH = 362.3e6 * 8  # bytes, see profiles/half_step_split_3d_m3.md
-FP32_NOMINAL_TOPS = 148 * 128 * 2032e6 / 1e12  # FP32 operations per second, nominal
+# Algorithmic HBM bytes of one half-step: every node's (Nu + Nv) coefficients
+# read once from the source grid and written once to the target grid, 8 bytes
+# each in both arithmetics (FP64, or an FP32 hi + lo pair).
+ALG_BYTES_PER_LAUNCH = 2 * DOF_PER_HALF * 8
+# DRAM read + write bytes per launch from ncu captures of the same kernels at
+# 64^3, scaled to 128^3 by the node count
+TRAFFIC_PER_LAUNCH = 373.8e6 * 8
+SPLIT_TRAFFIC_PER_LAUNCH = 362.3e6 * 8
+# FP32 operations the compensated (hi + lo) arithmetic spends per node: 12 per
+# multiply-add of an operator row, 8 per addition of the corner transform
 SPLIT_OPS_PER_NODE = (NU + NV) * (NU + NV) * 12 + (NU + NV) * D * (1 << D) * 8
 
 
@@ -169,28 +175,92 @@ def cpu_baseline_sample(u0, v0, n_targets, seed=1):
     return n_targets * (NU + NV) / dt, dt
 
 
+_POOL_STATE = {}
+
+
+def _pool_sample(job):
+    """One worker's share of an all-cores oracle sample (state inherited by fork)."""
+    seed, n_targets = job
+    return cpu_baseline_sample(_POOL_STATE["u0"], _POOL_STATE["v0"], n_targets, seed)[1]
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+class OraclePool:
+    """The oracle on every host core: one forked worker per core, each taking
+    its own random target nodes.  Fork before the process makes any CUDA call
+    (the workers inherit the initial state without copying it)."""
+
+    def __init__(self, u0, v0):
+        import multiprocessing as mp
+
+        _POOL_STATE["u0"], _POOL_STATE["v0"] = u0, v0
+        self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("fork").Pool(self.cores)
+
+    def sample(self, per_core, seed):
+        """All cores, per_core target nodes each: (DOF-updates/s, wall seconds)."""
+        t0 = time.perf_counter()
+        self.pool.map(_pool_sample, [(seed + i, per_core) for i in range(self.cores)], chunksize=1)
+        wall = time.perf_counter() - t0
+        return self.cores * per_core * (NU + NV) / wall, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(u0, v0):
+    """The oracle as it stands, on the host: single-threaded (8192 random dual
+    nodes of the workload, one half-step each) and on every core (4096 nodes per
+    core).  Runs before any CUDA call."""
+    v1, s1 = cpu_baseline_sample(u0, v0, 8192, seed=1)
+    pool = OraclePool(u0, v0)
+    try:
+        pool.sample(64, seed=1000)  # start-up
+        va, sa = pool.sample(4096, seed=2000)
+    finally:
+        pool.close()
+    return {"value": va, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "single_core_value": v1, "cpu_model": cpu_model(), "nproc": pool.cores,
+            "sample": f"one half-step of random dual nodes of the same 128^3 grid: {pool.cores} cores x 4096 nodes "
+                      f"({sa:.1f} s wall); single core 8192 nodes ({s1:.1f} s)"}
+
+
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    """Reference arm: the FP64 CPU oracle timed on every host core."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     u0, v0 = initial_state()
-    n_targets = 2048
-    for _ in range(args.warmup):
-        cpu_baseline_sample(u0, v0, 256)
-    times, vals = [], []
-    for k in range(args.steps):
-        v, dt = cpu_baseline_sample(u0, v0, n_targets, seed=10 + k)
-        vals.append(v)
-        times.append(dt)
-    value = n_targets * (NU + NV) * len(times) / sum(times)
+    pool = OraclePool(u0, v0)
+    per_core = 1024
+    try:
+        for k in range(args.warmup):
+            pool.sample(128, seed=500 * (k + 1))
+        times = [pool.sample(per_core, seed=10_000 * (k + 1))[1] for k in range(args.steps)]
+    finally:
+        pool.close()
+    units = pool.cores * per_core * (NU + NV)
+    value = units * len(times) / sum(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{n_targets} random dual nodes, one half-step each"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{n_targets} random target nodes x {args.steps} steps of one half-step"},
+        "config": {"workload": WORKLOAD,
+                   "sample": f"per step {pool.cores} cores x {per_core} random dual nodes, one half-step each"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                         "cpu_model": cpu_model(),
+                         "sample": f"{pool.cores} x {per_core} random target nodes x {args.steps} steps of one "
+                                   f"half-step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -247,19 +317,56 @@ def measure(hb, torch, dev, u0, v0, precision, args, ws, want_clocks):
             "clocks": clk.summary() if want_clocks else None}
 
 
+ACC_STEPS = 200      # full steps of the 3-D pulse workload
+ACC_CELLS = 2048     # cells sampled for the L2 errors (the same cells for every arithmetic)
+
+
+def accuracy(hb, torch, dev, u0, v0, precision):
+    """Relative L2 error against the exact solution after the workload's 200
+    full steps, by Gauss quadrature (2m+2 points per axis, exact for the
+    squared interpolant) over ACC_CELLS seeded random cells; the exact
+    solution (radial d'Alembert over periodic images) is evaluated on the
+    device."""
+    from paper_1802_05246_b300 import inputs as I
+
+    h = 1.0 / N
+    g = hb.Hermite(D, M, N, 1.0, h, LAM * h, hb.DISSIPATIVE, hb.PERIODIC, precision=precision)
+    du = torch.from_numpy(u0).to(dev)
+    dv = torch.from_numpy(v0).to(dev)
+    g.set_state_device(du, dv)
+    del du, dv
+    g.step(ACC_STEPS)
+    T = g.time
+    x, w = np.polynomial.legendre.leggauss(2 * M + 2)
+    xq, wq = 0.5 * x, 0.5 * w
+    cells = np.sort(np.random.default_rng(12345).choice(NODES, ACC_CELLS, replace=False))
+    ax = I.axis_coords(N, h, I.PERIODIC, 1)  # cells of the primal level: centred at dual nodes
+    ci = np.stack(np.unravel_index(cells, (N,) * D), -1)
+    Q = np.stack(np.meshgrid(*([xq * h] * D), indexing="ij"), -1).reshape(-1, D)
+    pts = torch.from_numpy(ax[ci][:, None, :] + Q[None, :, :]).to(dev)
+    cen, wid, amp = I.pulses_3d_config(0)
+    ex = I.pulse_wave_3d(pts, T, cen, wid, amp, xp=torch).contiguous()
+    e2, n2 = g.l2_error(0, xq, wq, ex, torch.from_numpy(cells.astype(np.int64)).to(dev))
+    g.close()
+    return float(np.sqrt(e2 / n2)), T
+
+
 def run_ours(args):
+    ws, rank, local = dist_env()
+    u0, v0 = initial_state()
+    # the oracle on the host cores, before this process makes any CUDA call
+    cpu = cpu_baseline(u0, v0) if (ws == 1 and rank == 0 and not args.no_cpu_baseline) else None
+
     import torch
 
     import paper_1802_05246_b300 as hb
 
-    ws, rank, local = dist_env()
     torch.cuda.set_device(local)  # before the process group, so NCCL binds this rank's GPU
     if ws > 1:
         import torch.distributed as dist
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
-    u0, v0 = initial_state()
 
     fp64 = measure(hb, torch, dev, u0, v0, hb.FP64, args, ws, False)
     split = measure(hb, torch, dev, u0, v0, hb.SPLIT32, args, ws, True)
@@ -296,18 +403,35 @@ def run_ours(args):
     e2e_value = job_throughput(dof_per_step, ws, 1e3 * e2e_s)
     state_bytes = NODES * (NU + NV) * 8
     g.close()
+    del hu, hv, ou, ov
+
+    # matched L2 error: both arithmetics against the exact solution after the
+    # workload's 200 steps (untimed)
+    err64, T = accuracy(hb, torch, dev, u0, v0, hb.FP64)
+    errsp, _ = accuracy(hb, torch, dev, u0, v0, hb.SPLIT32)
 
     if rank != 0:
         return 0
     pk = peaks()
-    # split half-step: FP32-pipe operations of the compensated algorithm per node
-    # (one operator row per output: nci*nco multiply-adds of 12 FP32 ops each,
-    # plus the corner transform: nci*d*2^d additions of 8 FP32 ops each)
-    ops_per_launch = NODES * SPLIT_OPS_PER_NODE
-    achieved = ops_per_launch / (split["half_ms"] / 1e3) / 1e12
-    flops64 = NODES * FLOP_PER_NODE
-    achieved64 = flops64 / (fp64["half_ms"] / 1e3) / 1e12
-    cpu_v, cpu_s = cpu_baseline_sample(u0, v0, 4096) if ws == 1 else (None, None)
+    hbm = pk.get("hbm_gbs")
+    probe32 = hb.peak_probe(2) / 1e12  # packed FP32 pairs, the split kernel's form
+    probe64 = hb.peak_probe(0) / 1e12
+
+    def roofline(kernel, launch_ms, traffic, pipe, probe, impl_ops=None):
+        achieved = ALG_BYTES_PER_LAUNCH / (launch_ms / 1e3) / 1e9
+        method = NODES * FLOP_PER_NODE / (launch_ms / 1e3) / 1e12
+        r = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+             "frac": achieved / hbm if hbm else None, "traffic": traffic,
+             "algorithmic_bytes_per_launch": ALG_BYTES_PER_LAUNCH, "launch_ms": launch_ms,
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+             "compute": {"pipe": pipe, "method_flop_per_launch": NODES * FLOP_PER_NODE, "method_tflops": method,
+                         "probe_peak_tflops": probe, "method_frac_of_probe": method / probe,
+                         "peak_source": "probe: hermite_peak_probe, FMA chains on this GPU"}}
+        if impl_ops:
+            r["compute"]["impl_ops_per_launch"] = impl_ops
+            r["compute"]["impl_tops"] = impl_ops / (launch_ms / 1e3) / 1e12
+        return r
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": split["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -318,34 +442,28 @@ def run_ours(args):
                    "step": "8 full time steps (16 half-steps) + 1 energy reduction",
                    "l2": "inputs larger than L2 (3.05 GB read+written per half-step vs 126 MB)",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "alu", "kernel": "half_step_split_kernel<3,12,10>", "achieved": achieved,
-                     "peak": FP32_NOMINAL_TOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_NOMINAL_TOPS,
-                     "peak_source": "FP32 pipe nominal (148 SMs x 128 lanes x 2.032 GHz, operations/s); "
-                                    "MEASURED_PEAKS.json has no FP32 entry",
-                     "ops_per_launch": ops_per_launch, "launch_ms": split["half_ms"],
-                     "hbm_GBps_equiv": 2 * DOF_PER_HALF * 8 / (split["half_ms"] / 1e3) / 1e9,
-                     "hbm_peak_GBps": pk.get("hbm_gbs"),
-                     # dram read+write per launch from an ncu capture of the same kernel at
-                     # 64^3 (scaled by the node count)
-                     "traffic": SPLIT_TRAFFIC_PER_LAUNCH},
+        "roofline": roofline("half_step_split_kernel<3,12,10>", split["half_ms"], SPLIT_TRAFFIC_PER_LAUNCH,
+                             "FP32 (packed pairs)", probe32, NODES * SPLIT_OPS_PER_NODE),
+        "accuracy": {"l2_err_fp64": err64, "l2_err_split": errsp, "ratio_split_over_fp64": errsp / err64,
+                     "bar": "split <= 1.2 x fp64 where fp64 >= 1e-9", "meets_bar": errsp <= 1.2 * err64,
+                     "t": T, "full_steps": ACC_STEPS,
+                     "measure": f"relative L2 of the I_m interpolant vs the exact solution, {ACC_CELLS} sampled "
+                                f"cells, {2 * M + 2}^3 Gauss points each"},
         "fp64": {"value": value64, "ms_per_step": fp64["ms"] / args.steps, "dtype": "f64",
-                 "roofline": {"bound": "alu", "kernel": "half_step_f64_kernel<3,92>", "achieved": achieved64,
-                              "peak": FP64_NOMINAL_GFLOPS / 1e3, "unit": "TFLOP/s",
-                              "frac": achieved64 / (FP64_NOMINAL_GFLOPS / 1e3), "launch_ms": fp64["half_ms"],
-                              "traffic": TRAFFIC_PER_LAUNCH},
-                 "energy_last": [float(x) for x in fp64["energy"]]},
+                 "roofline": roofline("half_step_f64_kernel<3,92>", fp64["half_ms"], TRAFFIC_PER_LAUNCH, "FP64",
+                                      probe64),
+                 "energy_plain_last": float(fp64["energy"][0])},
         "split_vs_fp64_rel_l2": split_vs_fp64,
-        "cpu_baseline": ({"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                          "sample": f"4096 random dual nodes of the same grid, one half-step ({cpu_s:.1f} s)"}
-                         if cpu_v else None),
+        "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes + 24},
         # per step: one half-step kernel per half-step, then the energy: one
         # sum-factorised kernel (both forms) and two partial-sum reductions
         "gpu_launches": (2 * FULL_STEPS_PER_STEP + 3) * args.steps,
         "clocks": split["clocks"],
-        "energy_last": [float(x) for x in split["energy"]],
+        # the plain energy int v^2 + c^2 |grad u|^2; the invariant (seminorm)
+        # energy of smooth fine-grid data is rounding-level and not reported here
+        "energy_plain_last": float(split["energy"][0]),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -592,6 +710,75 @@ def run_learned(args):
     return 0
 
 
+NCU_CASES = ("half_step_f64", "half_step_split", "energy_f64", "energy_split", "batch_f64", "batch_split", "conv")
+
+
+def run_ncu_case(args):
+    """Small, self-contained cases for Nsight Compute captures (not benchmarks;
+    no timing is printed):
+      half_step_f64 / half_step_split: 3-D m=3, 64^3 periodic, c dt/h = 0.9,
+        random device data (~380 MB moved per half-step, above the L2), three
+        half-steps of --variant (0 full dissipative, 1 conservative, 2 simple);
+      energy_f64 / energy_split: the same grid, one energy call (both forms);
+      batch_f64 / batch_split: the first 128 problems of the seed-0 ragged 2-D
+        workload (dissipative), two full steps at the item size and blocks per
+        SM the autotuner picks on the full workload (256 nodes; 2 blocks per
+        SM for FP64, 8 for split);
+      conv: 64 images of 128 x 128 x 64 channels in BF16 (134 MB), dilation 8,
+        three forward launches, then three weight-gradient launches."""
+    import torch
+
+    import paper_1802_05246_b300 as hb
+
+    torch.cuda.set_device(0)
+    case = args.ncu_case
+    if case.startswith(("half_step", "energy")):
+        n, m = 64, 3
+        h = 1.0 / n
+        prec = hb.FP64 if case.endswith("f64") else hb.SPLIT32
+        variant = args.variant if case.startswith("half_step") else hb.DISSIPATIVE
+        g = hb.Hermite(3, m, n, 1.0, h, 0.9 * h, variant, hb.PERIODIC, precision=prec)
+        u = torch.randn(n ** 3, (m + 1) ** 3, dtype=torch.float64, device="cuda")
+        v = torch.randn(n ** 3, m ** 3, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        g.set_state_device(u, v)
+        if case.startswith("half_step"):
+            g.advance_half(3)
+        else:
+            g.energy()
+        torch.cuda.synchronize()
+        g.close()
+    elif case.startswith("batch"):
+        fp64 = case == "batch_f64"
+        probs = [(2, m, Np, 1.0, 1.0 / Np, 0.9 / Np, hb.DISSIPATIVE, bc)
+                 for (Np, m, bc, _, _, _) in batch_problems()[:128]]
+        b = hb.HermiteBatch(probs, precision=hb.FP64 if fp64 else hb.SPLIT32)
+        b.set_stream(torch.cuda.Stream())
+        b.config(256, 2 if fp64 else 8)
+        b.step(2)
+        torch.cuda.synchronize()
+        b.close()
+    else:
+        B, C, dil = 64, 64, 8
+        L = hb.lib()
+        s = torch.cuda.current_stream().cuda_stream
+        x = torch.randn((B, 128, 128, C), device="cuda").to(torch.bfloat16)
+        dy = torch.randn((B, 128, 128, C), device="cuda").to(torch.bfloat16)
+        w = (torch.randn((C, 9, C), device="cuda") * 0.05).to(torch.bfloat16)
+        y = torch.empty_like(x)
+        dw = torch.zeros((C, 9, C), device="cuda")
+        for _ in range(3):
+            if L.hnn_conv3x3_fwd(x.data_ptr(), w.data_ptr(), None, None, B, 128, 128, C, C, dil, 1, y.data_ptr(),
+                                 None, s):
+                raise RuntimeError("hnn_conv3x3_fwd failed")
+        for _ in range(3):
+            if L.hnn_conv3x3_wgrad(x.data_ptr(), dy.data_ptr(), B, 128, 128, C, C, dil, dw.data_ptr(), s):
+                raise RuntimeError("hnn_conv3x3_wgrad failed")
+        torch.cuda.synchronize()
+    print("ncu case", case, "ok", flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,7 +788,13 @@ def main():
     ap.add_argument("--workload", default="grid3d", choices=["grid3d", "batch2d", "learned2d", "paper3d"])
     ap.add_argument("--weights", default=LEARNED_WEIGHTS, help="learned2d: trained super-stepper")
     ap.add_argument("--bar", type=float, default=1e-3, help="learned2d: accepted rel. L2 error")
+    ap.add_argument("--ncu-case", choices=NCU_CASES, default=None,
+                    help="run one small case for an Nsight Compute capture instead of a benchmark")
+    ap.add_argument("--variant", type=int, default=0, help="--ncu-case half_step_*: method variant")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing on the host cores")
     args = ap.parse_args()
+    if args.ncu_case:
+        return run_ncu_case(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch2d":

@@ -133,9 +133,33 @@ int hermite_advance_half(hermite_ctx *ctx, int64_t nhalf);
 /* Number of half-steps taken since the state was set. */
 int64_t hermite_half_steps(const hermite_ctx *ctx);
 
-/* Time of the primal level: (half-steps / 2) * dt rounded down to whole steps
- * for the conservative method, half-steps * dt/2 for the dissipative one. */
+/* Time of the primal level.  Dissipative: half-steps * dt/2 (the newest
+ * level, primal after an even count).  Conservative: ((half-steps + 1) / 2) * dt
+ * in integer division, i.e. half-steps * dt/2 rounded UP to a whole step: the
+ * first half-step updates the primal level from t = 0 to t = dt, the second
+ * the dual level from dt/2 to 3dt/2, and so on. */
 double hermite_time(const hermite_ctx *ctx);
+
+/* L2 error of the cell interpolant against an exact solution (Sec. 5.1: the
+ * piecewise I_m interpolant of the u data, degree 2m+1 per axis, compared with
+ * the exact solution at quadrature points), reduced in FP64 on the device.
+ *   grid    grid holding the u level (cells are centred at the nodes of the
+ *           other grid; ghost polynomials and half cells at non-periodic
+ *           boundaries as for the energies)
+ *   cells   device pointer to ncells cell indices (nodes of grid 1-grid, C
+ *           order), or NULL for every cell in order (ncells must then equal
+ *           hermite_nodes(ctx, 1-grid)); indices outside [0, nodes) are
+ *           skipped
+ *   nq, xq, wq  host arrays: nq <= 16 quadrature points per axis in cell
+ *           units (xi in [-1/2, 1/2]) and weights summing to 1
+ *   exact   device pointer [ncells][nq^d]: the exact u at the points
+ *           centre + h (xq[i_0], .., xq[i_{d-1}]), C order over the axes
+ *   out     host: out[0] = sum over the cells of the quadrature of
+ *           (I_m u - exact)^2, out[1] = the same of exact^2 (both include h^d)
+ * Split contexts use their hi + lo level.  Allocates a small device buffer and
+ * synchronises the context's stream.  HERMITE_ERR_ARG for bad arguments. */
+int hermite_l2_error(hermite_ctx *ctx, int grid, int64_t ncells, const int64_t *cells, int nq, const double *xq,
+                     const double *wq, const double *exact, double out[2]);
 
 /* Primal-grid state, host buffers [nodes_primal][Nu] / [nodes_primal][Nv]
  * (v may be NULL; ignored for the conservative method).  Dissipative: valid
@@ -196,12 +220,25 @@ int hermite_operator(hermite_ctx *ctx, int which, double *out, int *rows, int *c
  *            dissipative: [int v^2 + c^2|grad u|^2, stable1/stable2 energy];
  *            conservative: [|p|^2_{m+1,..,m+1}, c^2 int |grad p|^2].
  * Limit: at most 2^21 cells (= nodes of the other grid); larger problems get
- * HERMITE_ERR_ARG with a message.  No host synchronisation.  The first call
+ * HERMITE_ERR_ARG with a message; a context without energy forms (a batch
+ * problem) gets HERMITE_ERR_STATE, as from hermite_energy.  No host
+ * synchronisation.  The first call
  * on a device looks up the array's device address (make that first call
  * before any stream capture).  All calls share the one array: calls whose
  * work overlaps on the GPU (other streams or threads) race and must be
  * serialised by the caller.  The context's device must be current. */
 int hermite_energy_noalloc(hermite_ctx *ctx, int grid, const double *level, int64_t ld, double *out_dev);
+
+/* Measured FMA throughput of the current device, for roofline denominators
+ * (the paper has no counterpart: a measurement aid).  kind 0: FP64 FMA,
+ * 1: FP32 FMA, 2: FP32 FMA on packed pairs (two per instruction, the form the
+ * split-precision kernels issue).  Eight independent FMA chains per thread
+ * over 8 blocks of 256 threads per SM, timed with CUDA events on a private
+ * stream after one warm-up launch; *flops_per_s counts an FMA as 2 flops.
+ * Allocates and frees a small device buffer; synchronises that stream.
+ * HERMITE_ERR_ARG for a NULL pointer or unknown kind, HERMITE_ERR_CUDA on a
+ * CUDA failure (then *flops_per_s = 0). */
+int hermite_peak_probe(int kind, double *flops_per_s);
 
 /* ------------------------------------------------------------------------
  * Ragged batches.  Many independent problems -- differing N, m, boundary

@@ -30,7 +30,8 @@ EXPORTS = [
     "hermite_create", "hermite_destroy", "hermite_set_stream", "hermite_set_state", "hermite_set_state_device",
     "hermite_set_state2", "hermite_step", "hermite_advance_half", "hermite_half_steps", "hermite_time",
     "hermite_get_state", "hermite_get_grid", "hermite_set_grid", "hermite_get_grid_device", "hermite_energy",
-    "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error", "hermite_energy_noalloc",
+    "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error", "hermite_energy_noalloc", "hermite_peak_probe",
+    "hermite_l2_error",
     "hermite_create_ex", "hermite_batch_create", "hermite_batch_destroy", "hermite_batch_problem",
     "hermite_batch_set_stream", "hermite_batch_step", "hermite_batch_dof_per_step", "hermite_batch_autotune",
     "hermite_batch_config", "hermite_batch_last_error", "hermite_batch_get_states_device",
@@ -83,6 +84,8 @@ def lib():
         "hermite_operator": (c_int, [vp, c_int, vp, ip, ip]),
         "hermite_last_error": (ctypes.c_char_p, [vp]),
         "hermite_energy_noalloc": (c_int, [vp, c_int, vp, i64, vp]),
+        "hermite_peak_probe": (c_int, [c_int, ctypes.POINTER(c_dbl)]),
+        "hermite_l2_error": (c_int, [vp, c_int, i64, vp, c_int, dp, dp, vp, dp]),
         "hermite_create_ex": (c_int, [c_int, c_int, i64, c_dbl, c_dbl, c_dbl, c_int, c_int, c_int, ctypes.POINTER(vp)]),
         "hermite_batch_create": (c_int, [c_int, vp, vp, vp, vp, vp, vp, vp, vp, c_int, ctypes.POINTER(vp)]),
         "hermite_batch_destroy": (None, [vp]),
@@ -238,6 +241,26 @@ class Hermite:
         level: coefficient-major float64 device tensor, out: 2-element device tensor."""
         self._check(lib().hermite_energy_noalloc(self._h, int(grid), _ptr(level), int(ld), _ptr(out)))
 
+    def l2_error(self, grid, xq, wq, exact, cells=None):
+        """(sum of (I_m u - exact)^2, sum of exact^2) over cells by quadrature
+        (see hermite_l2_error).  xq, wq: 1-D points on [-1/2, 1/2] and weights
+        summing to 1; exact: float64 device tensor [ncells, nq^d]; cells: int64
+        device tensor of cell indices, or None for every cell."""
+        xq = np.ascontiguousarray(xq, dtype=np.float64)
+        wq = np.ascontiguousarray(wq, dtype=np.float64)
+        out = (ctypes.c_double * 2)()
+        ncells = int(exact.shape[0])
+        if str(exact.dtype) != "torch.float64" or int(exact.numel()) != ncells * int(xq.size) ** self.d:
+            raise ValueError("exact: float64 device tensor [ncells, nq^d]")
+        if cells is not None:
+            if str(cells.dtype) != "torch.int64" or not cells.is_contiguous() or int(cells.numel()) != ncells:
+                raise ValueError("cells: a contiguous int64 device tensor with one entry per row of exact")
+        cptr = None if cells is None else cells.data_ptr()
+        self._check(lib().hermite_l2_error(self._h, int(grid), ncells, cptr, int(xq.size),
+                                           xq.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           wq.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(exact), out))
+        return out[0], out[1]
+
     def operator(self, which=0):
         r, c = ctypes.c_int(), ctypes.c_int()
         self._check(lib().hermite_operator(self._h, which, None, ctypes.byref(r), ctypes.byref(c)))
@@ -257,6 +280,16 @@ def _borrow(handle, d, m, N, c, h, dt, variant, bc, precision):
     lib().hermite_ncoef(g._h, ctypes.byref(nu), ctypes.byref(nv))
     g.Nu, g.Nv = nu.value, nv.value
     return g
+
+
+def peak_probe(kind):
+    """Measured FMA throughput (flop/s, an FMA = 2) of the current device:
+    kind 0 FP64, 1 FP32, 2 FP32 packed pairs (see hermite_peak_probe)."""
+    out = ctypes.c_double()
+    rc = lib().hermite_peak_probe(int(kind), ctypes.byref(out))
+    if rc != 0:
+        raise HermiteError(rc, "hermite_peak_probe failed")
+    return out.value
 
 
 class HermiteBatch:

@@ -404,6 +404,15 @@ double hermite_time(const hermite_ctx *ctx) {
   return (double)ctx->half * 0.5 * ctx->dt;
 }
 
+int hermite_l2_error(hermite_ctx *ctx, int grid, int64_t ncells, const int64_t *cells, int nq, const double *xq,
+                     const double *wq, const double *exact, double out[2]) {
+  if (!ctx) return HERMITE_ERR_ARG;
+  if ((grid != 0 && grid != 1) || !xq || !wq || !exact || !out)
+    return fail(ctx, HERMITE_ERR_ARG, "hermite_l2_error: bad grid or NULL pointer");
+  if (int rc = sync_fp64_from_split(ctx, grid)) return rc;
+  return launch_l2_error(ctx, grid, ncells, cells, nq, xq, wq, exact, out);
+}
+
 int hermite_get_state(hermite_ctx *ctx, double *u, double *v) {
   if (!ctx) return HERMITE_ERR_ARG;
   if (!u) return fail(ctx, HERMITE_ERR_ARG, "u is NULL");

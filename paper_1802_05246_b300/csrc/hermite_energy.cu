@@ -308,9 +308,15 @@ int launch_energy_noalloc_d(hermite_ctx *ctx, const Geometry &g, int form, const
                             double *out) {
   const int nq = ctx->nq[form];
   const size_t smem = sizeof(double) * ((size_t)nq * nq + (size_t)nq * kEThreads) + nq + 16;
-  if (!cuda_ok(ctx, cudaFuncSetAttribute(energy_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
-               "cudaFuncSetAttribute energy"))
-    return HERMITE_ERR_CUDA;
+  // the shared-memory opt-in is a host driver call: once per device and thread
+  static thread_local int configured_dev = -1;
+  if (configured_dev != ctx->device) {
+    if (!cuda_ok(ctx,
+                 cudaFuncSetAttribute(energy_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
+                 "cudaFuncSetAttribute energy"))
+      return HERMITE_ERR_CUDA;
+    configured_dev = ctx->device;
+  }
   const int64_t blocks = std::max<int64_t>(1, (g.nodes_dst + kEThreads - 1) / kEThreads);
   dim3 grid((unsigned)blocks, (unsigned)(1 << D));
   energy_kernel<D><<<grid, kEThreads, smem, ctx->stream>>>(g, ctx->Q[form], nq, ctx->par_in, A, A, partials);
@@ -328,6 +334,10 @@ extern "C" int hermite_energy_noalloc(hermite_ctx *ctx, int grid, const double *
   if ((grid != 0 && grid != 1) || !level || !out_dev || ld < ctx->nodes[grid]) {
     ctx->err = "hermite_energy_noalloc: bad grid, NULL pointer or ld < nodes";
     return HERMITE_ERR_ARG;
+  }
+  if (!ctx->has_energy) {
+    ctx->err = "this context was created without energy forms";
+    return HERMITE_ERR_STATE;
   }
   // cells of a level held on grid g are centred at the nodes of grid 1-g
   const int64_t cells = ctx->nodes[1 - grid];

@@ -128,6 +128,12 @@ int launch_energy_tp_pair(hermite_ctx *ctx, int grid, const void *A, const void 
 int launch_energy_tp_level(hermite_ctx *ctx, int grid, const double *level, int64_t ld, double *partials,
                            int64_t partials_len, double *out);
 
+// L2 error of the I_m interpolant of the FP64 u level on `grid` against
+// exact values at tensor quadrature points (hermite_error.cu); cells and
+// exact are device pointers, xq / wq host arrays; synchronises the stream.
+int launch_l2_error(hermite_ctx *ctx, int grid, int64_t ncells, const int64_t *cells, int nq, const double *xq,
+                    const double *wq, const double *exact, double out[2]);
+
 Geometry make_geometry(const hermite_ctx *ctx, int dst);
 int create_context(int d, int m, int64_t N, double c, double h, double dt, int variant, int bc, int precision,
                    bool with_energy, hermite_ctx **out);

@@ -159,3 +159,59 @@ def superstep_pulses(traj: int):
     centres U[0,1)^2, widths U[0.05,0.15], amplitudes N(0,1), drawn from
     numpy's PCG64 seeded with traj."""
     return random_pulses(np.random.default_rng(traj), 2, 1, 6, 0.05, 0.15)
+
+
+def pulse_wave_3d(points, t, centres, widths, amps, c=1.0, L=1.0, xp=np):
+    """Exact solution u(x, t) of u_tt = c^2 Lap u on the periodic cube [0, L)^3
+    with u(x, 0) = sum_p A_p sum_{n in Z^3} g_p(|x - x_p - n L|),
+    g_p(r) = exp(-r^2 / w_p^2), and u_t(x, 0) = 0 (the 3-D pulse workload).
+
+    Every periodic image is a radial pulse.  For radial data r*u solves the 1-D
+    wave equation in r with an odd extension, so d'Alembert's formula gives
+        u(r, t) = [(r - ct) g(r - ct) + (r + ct) g(r + ct)] / (2 r),
+    whose limit at r = 0 is W'(ct) with W(s) = s g(s); for r below 1e-4 w the
+    two-term Taylor series W'(ct) + W'''(ct) r^2 / 6 replaces the quotient.
+    Images farther than 6.8 w from the sphere r = ct contribute below 1e-20
+    and are skipped.
+
+    points: [..., 3] array (numpy, or a torch tensor with xp=torch); returns
+    an array of the leading shape."""
+    centres = np.asarray(centres, dtype=np.float64).reshape(-1, 3)
+    ct = c * float(t)
+    out = xp.zeros_like(points[..., 0])
+    for p in range(centres.shape[0]):
+        w = float(widths[p])
+        R = 6.8 * w
+        K = int(math.ceil((ct + R) / L)) + 1
+        d0 = points - xp.asarray(centres[p]) if xp is np else points - xp.tensor(centres[p], dtype=points.dtype,
+                                                                                    device=points.device)
+        # bounding box of the offsets: images whose distance range over the
+        # box misses the shell |r - ct| <= R (and the ball r + ct <= R) are
+        # skipped
+        lo = [float(d0[..., i].min()) for i in range(3)]
+        hi = [float(d0[..., i].max()) for i in range(3)]
+        for n0 in range(-K, K + 1):
+            for n1 in range(-K, K + 1):
+                for n2 in range(-K, K + 1):
+                    shift = (n0 * L, n1 * L, n2 * L)
+                    near2 = far2 = 0.0
+                    for i in range(3):
+                        a0, a1 = lo[i] - shift[i], hi[i] - shift[i]
+                        near2 += 0.0 if a0 <= 0.0 <= a1 else min(a0 * a0, a1 * a1)
+                        far2 += max(a0 * a0, a1 * a1)
+                    if math.sqrt(near2) > ct + R or (math.sqrt(far2) < ct - R and math.sqrt(far2) + ct > R):
+                        continue
+                    r2 = (d0[..., 0] - shift[0]) ** 2 + (d0[..., 1] - shift[1]) ** 2 + (d0[..., 2] - shift[2]) ** 2
+                    r = xp.sqrt(r2)
+                    a, b = r - ct, r + ct
+                    far = (xp.abs(a) > R) & (b > R)
+                    small = r < 1e-4 * w
+                    rs = xp.where(small, xp.ones_like(r), r)
+                    quo = (a * xp.exp(-(a * a) / (w * w)) + b * xp.exp(-(b * b) / (w * w))) / (2.0 * rs)
+                    g = math.exp(-(ct * ct) / (w * w))
+                    w1 = (1.0 - 2.0 * ct * ct / (w * w)) * g
+                    w3 = (24.0 * ct * ct / w ** 4 - 6.0 / (w * w) - 8.0 * ct ** 4 / w ** 6) * g
+                    ser = w1 + w3 * r2 / 6.0
+                    val = xp.where(small, ser, quo)
+                    out = out + float(amps[p]) * xp.where(far, xp.zeros_like(val), val)
+    return out

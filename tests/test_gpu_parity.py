@@ -488,3 +488,18 @@ def test_error_statuses(hb, orc):
     with pytest.raises(hb.HermiteError) as e:
         g.step(-1)
     assert e.value.code == -1
+
+
+def test_time_of_the_primal_level(hb, orc):
+    """hermite_time: dissipative half * dt/2; conservative ((half + 1) / 2) * dt
+    (the first half-step moves the primal level from 0 to dt)."""
+    N, dt = 8, 0.1
+    for variant, want in ((0, [0, 0.05, 0.1, 0.15, 0.2]), (1, [0, 0.1, 0.1, 0.2, 0.2])):
+        g = hb.Hermite(1, 2, N, 1.0, 1.0 / N * 2, dt, variant, 0)
+        g.set_state(np.zeros((N, 3)), np.zeros((N, 2)) if variant == 0 else None)
+        got = []
+        for k in range(5):
+            got.append(g.time)
+            g.advance_half(1)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+        g.close()

@@ -8,6 +8,7 @@ import pytest
 from numpy.polynomial import Polynomial
 
 from paper_1802_05246_b300 import inputs as I
+from tests.gpu_util import hermite_cond
 
 
 def _sin_state(d, m, N, a, grid=0, bc=I.PERIODIC):
@@ -149,3 +150,85 @@ def test_conserved_variables_identity(orc, m):
             total += integ(h / 4) - integ(0.0)
     G = P.cons_G(p, q)
     np.testing.assert_allclose(total, 2 * G, rtol=1e-10)
+
+
+# ----------------------------------------------- d > 1: Eq. (stable2)
+def _stable2_exact(d, m, wu, wv, c):
+    """Limit of the Sec. 3.3 functional c^2 sum_i |d_i I^(i) u|^2_{m..m} +
+    |I_{m-1} v|^2_{m..m} for u = prod sin(wu_i x_i), v = prod sin(wv_i x_i) on
+    the unit cube: c^2 sum_i int (d_i^{m+1} prod_{j!=i} d_j^m u)^2 +
+    int (prod_j d_j^m v)^2, every square of a product of sines or cosines
+    integrating to 2^-d."""
+    e = 0.0
+    for i in range(d):
+        t = c * c
+        for j in range(d):
+            t *= wu[j] ** (2 * (m + 1) if j == i else 2 * m)
+        e += t
+    t = 1.0
+    for j in range(d):
+        t *= wv[j] ** (2 * m)
+    return (e + t) / 2**d
+
+
+@pytest.mark.parametrize("d,m,N1,N2", [(2, 1, 16, 32), (2, 2, 16, 32), (2, 3, 16, 32), (3, 1, 8, 16), (3, 2, 8, 16),
+                                       (3, 3, 6, 8)])
+def test_stable2_functional_converges_to_its_closed_form(orc, d, m, N1, N2):
+    """The d > 1 invariant of or_diss_energy (out[1], Eq. stable2) tends to
+    its closed form as h -> 0, at the observed order 2m (the derivatives of
+    order m of the degree-(2m-1) interpolants converge at h^m, squared).  The
+    wave numbers differ per axis, so a derivative order given to the wrong
+    axis, a wrong power of h or a dropped term changes the limit itself."""
+    c = 1.3
+    wu = [2 * np.pi, 4 * np.pi, 2 * np.pi][:d]
+    wv = [4 * np.pi, 2 * np.pi, 6 * np.pi][:d]
+    exact = _stable2_exact(d, m, wu, wv, c)
+    errs = []
+    for N in (N1, N2):
+        h = 1.0 / N
+        P = orc.Problem(d, m, N, c, h, 0.5 * h / c, orc.DISSIPATIVE, orc.PERIODIC)
+        u = I.tensor_data([I.sine_data(1, m, N, h, 0, 0, [wu[i]]) for i in range(d)])
+        v = I.tensor_data([I.sine_data(1, m - 1, N, h, 0, 0, [wv[i]]) for i in range(d)])
+        errs.append(abs(P.diss_energy(0, u, v)[1] - exact) / exact)
+    order = np.log(errs[0] / errs[1]) / np.log(N2 / N1)
+    assert order >= 2 * m - 0.5, (errs, order)
+    assert errs[1] < (0.06 if m == 1 else 2e-3), errs
+
+
+# ------------------------------------------- long runs (Sec. 5.2, E2)
+@pytest.mark.parametrize("m", [1, 3, 5])
+@pytest.mark.parametrize("data", ["random", "sine"])
+def test_conservative_invariant_long_run(orc, m, data):
+    """Sec. 5.2: the conservative method conserves its energy to round-off over
+    long runs.  1-D periodic on [0, 2 pi), h = 2 pi / 30, dt = h/2, 10^4 full
+    steps, G checked every 10^3 steps.
+    Random U(0,1) coefficients: |G^n - G^0| <= sqrt(n) 1e-12 |G^0|.
+    sin x cos t: the seminorm of smooth data is carried by its top
+    coefficients, whose rounding in the oracle's LU solve (forward error
+    ~ eps * cond of the Eq. Hermcon system) accumulates step after step, so the
+    bound is linear: |G^n - G^0| <= n 8 eps cond |p|^2_{m+1}; for m = 5 the
+    state itself stays within 1e-9 of the exact solution."""
+    N = 30
+    h = 2 * np.pi / N
+    dt = h / 2
+    P = orc.Problem(1, m, N, 1.0, h, dt, orc.CONSERVATIVE, orc.PERIODIC)
+    if data == "random":
+        rng = np.random.default_rng(m)
+        p, q = rng.uniform(0, 1, (N, m + 1)), rng.uniform(0, 1, (N, m + 1))
+    else:
+        p = I.sine_data(1, m, N, h, 0, 0, [1.0])
+        q = np.cos(dt / 2) * I.sine_data(1, m, N, h, 0, 1, [1.0])
+    G0 = P.cons_G(p, q)
+    scale = P.cons_forms(0, p, p)[0]
+    n = 0
+    for _ in range(10):
+        p, q = P.run(p, nsteps=1000, dual_u=q)
+        n += 1000
+        dG = abs(P.cons_G(p, q) - G0)
+        if data == "random":
+            assert dG <= np.sqrt(n) * 1e-12 * abs(G0), (n, dG / abs(G0))
+        else:
+            assert dG <= n * 8 * np.finfo(float).eps * hermite_cond(m) * scale, (n, dG)
+    if data == "sine" and m == 5:
+        pe = np.cos(n * dt) * I.sine_data(1, m, N, h, 0, 0, [1.0])
+        assert np.linalg.norm(p - pe) <= 1e-9 * np.linalg.norm(pe)
