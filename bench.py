@@ -710,15 +710,16 @@ def run_learned(args):
     return 0
 
 
-NCU_CASES = ("half_step_f64", "half_step_split", "energy_f64", "energy_split", "batch_f64", "batch_split", "conv")
+NCU_CASES = ("half_step_f64", "half_step_split", "half_step_tc", "energy_f64", "energy_split", "batch_f64", "batch_split", "conv")
 
 
 def run_ncu_case(args):
     """Small, self-contained cases for Nsight Compute captures (not benchmarks;
     no timing is printed):
-      half_step_f64 / half_step_split: 3-D m=3, 64^3 periodic, c dt/h = 0.9,
+      half_step_f64 / half_step_split / half_step_tc: 3-D m=3, 64^3 periodic, c dt/h = 0.9,
         random device data (~380 MB moved per half-step, above the L2), three
         half-steps of --variant (0 full dissipative, 1 conservative, 2 simple);
+        the split cases on the CUDA-core and the tensor-core engine;
       energy_f64 / energy_split: the same grid, one energy call (both forms);
       batch_f64 / batch_split: the first 128 problems of the seed-0 ragged 2-D
         workload (dissipative), two full steps at the item size and blocks per
@@ -738,6 +739,8 @@ def run_ncu_case(args):
         prec = hb.FP64 if case.endswith("f64") else hb.SPLIT32
         variant = args.variant if case.startswith("half_step") else hb.DISSIPATIVE
         g = hb.Hermite(3, m, n, 1.0, h, 0.9 * h, variant, hb.PERIODIC, precision=prec)
+        if prec == hb.SPLIT32:
+            g.set_split_engine(1 if case == "half_step_tc" else 0)
         u = torch.randn(n ** 3, (m + 1) ** 3, dtype=torch.float64, device="cuda")
         v = torch.randn(n ** 3, m ** 3, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()

@@ -240,6 +240,31 @@ int hermite_energy_noalloc(hermite_ctx *ctx, int grid, const double *level, int6
  * CUDA failure (then *flops_per_s = 0). */
 int hermite_peak_probe(int kind, double *flops_per_s);
 
+/* Engine of a split-precision context's half-step (the operator and the
+ * arithmetic are the same, Sec. 3 / 4; the engines differ in how the FP32
+ * hi + lo products are formed):
+ *   0  CUDA cores: compensated FP32 multiply-adds on packed pairs (default);
+ *   1  tensor cores (tcgen05): exact products of BF16 digits of both operands
+ *      with FP32 accumulation, available where d >= 2 and every parity class
+ *      of inputs and of outputs is at most 16 coefficients wide (3-D m <= 3,
+ *      2-D m <= 4).
+ * HERMITE_ERR_STATE for an FP64 context, HERMITE_ERR_UNSUPPORTED if engine 1
+ * is asked for a shape it does not cover, HERMITE_ERR_ARG otherwise bad.
+ * hermite_get_split_engine returns the engine in use (-1: not a split context). */
+int hermite_set_split_engine(hermite_ctx *ctx, int engine);
+int hermite_get_split_engine(const hermite_ctx *ctx);
+
+/* Tensor-core self-test (the paper has no counterpart): one CTA computes
+ * D0 = A B^T and D1 = A B[0:N-16]^T with tcgen05.mma (BF16 operands in the
+ * no-swizzle K-major shared-memory layout of the tensor-core half-step, FP32
+ * accumulation in tensor memory, D1 at a column offset) for library-generated
+ * integer operands |a|, |b| <= 256, so that every exact partial sum is an
+ * integer below 2^24.  K in {16, 32, .., 128}, N in {32, 48, .., 96}.  Host
+ * buffers: A [128][K] and B [N][K] receive the operands, D0 [128][N] and
+ * D1 [128][N-16] the products.  HERMITE_ERR_TIMEOUT if the MMA completion wait
+ * ran out (bounded), HERMITE_ERR_ARG for bad sizes.  Synchronises the device. */
+int hermite_tc_selftest(int K, int N, float *A, float *B, float *D0, float *D1);
+
 /* ------------------------------------------------------------------------
  * Ragged batches.  Many independent problems -- differing N, m, boundary
  * condition, variant and time step, one dimension d for the whole batch --

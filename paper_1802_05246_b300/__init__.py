@@ -31,7 +31,7 @@ EXPORTS = [
     "hermite_set_state2", "hermite_step", "hermite_advance_half", "hermite_half_steps", "hermite_time",
     "hermite_get_state", "hermite_get_grid", "hermite_set_grid", "hermite_get_grid_device", "hermite_energy",
     "hermite_nodes", "hermite_ncoef", "hermite_operator", "hermite_last_error", "hermite_energy_noalloc", "hermite_peak_probe",
-    "hermite_l2_error",
+    "hermite_l2_error", "hermite_tc_selftest", "hermite_set_split_engine", "hermite_get_split_engine",
     "hermite_create_ex", "hermite_batch_create", "hermite_batch_destroy", "hermite_batch_problem",
     "hermite_batch_set_stream", "hermite_batch_step", "hermite_batch_dof_per_step", "hermite_batch_autotune",
     "hermite_batch_config", "hermite_batch_last_error", "hermite_batch_get_states_device",
@@ -86,6 +86,9 @@ def lib():
         "hermite_energy_noalloc": (c_int, [vp, c_int, vp, i64, vp]),
         "hermite_peak_probe": (c_int, [c_int, ctypes.POINTER(c_dbl)]),
         "hermite_l2_error": (c_int, [vp, c_int, i64, vp, c_int, dp, dp, vp, dp]),
+        "hermite_tc_selftest": (c_int, [c_int, c_int, vp, vp, vp, vp]),
+        "hermite_set_split_engine": (c_int, [vp, c_int]),
+        "hermite_get_split_engine": (c_int, [vp]),
         "hermite_create_ex": (c_int, [c_int, c_int, i64, c_dbl, c_dbl, c_dbl, c_int, c_int, c_int, ctypes.POINTER(vp)]),
         "hermite_batch_create": (c_int, [c_int, vp, vp, vp, vp, vp, vp, vp, vp, c_int, ctypes.POINTER(vp)]),
         "hermite_batch_destroy": (None, [vp]),
@@ -240,6 +243,14 @@ class Hermite:
         """Allocation-free energy of a device level (see hermite_energy_noalloc);
         level: coefficient-major float64 device tensor, out: 2-element device tensor."""
         self._check(lib().hermite_energy_noalloc(self._h, int(grid), _ptr(level), int(ld), _ptr(out)))
+
+    @property
+    def split_engine(self):
+        """Half-step engine of a split context: 0 CUDA cores, 1 tensor cores (-1: FP64)."""
+        return int(lib().hermite_get_split_engine(self._h))
+
+    def set_split_engine(self, engine):
+        self._check(lib().hermite_set_split_engine(self._h, int(engine)))
 
     def l2_error(self, grid, xq, wq, exact, cells=None):
         """(sum of (I_m u - exact)^2, sum of exact^2) over cells by quadrature

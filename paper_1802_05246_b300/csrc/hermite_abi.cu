@@ -82,6 +82,11 @@ void release(hermite_ctx *ctx) {
   cudaFree(ctx->pcls);
   cudaFree(ctx->tpm);
   cudaFree(ctx->tpmf);
+  cudaFree(ctx->tc_B);
+  cudaFree(ctx->tc_inb);
+  cudaFree(ctx->tc_orow);
+  cudaFree(ctx->tc_er);
+  cudaFree(ctx->tc_status);
 }
 
 bool is_split(const hermite_ctx *ctx) { return ctx->precision == HERMITE_SPLIT32; }
@@ -170,7 +175,7 @@ int download_grid(hermite_ctx *ctx, int grid, double *u, double *v, bool device_
       !cuda_ok(ctx, cudaMemcpyAsync(v, sv, sizeof(double) * nodes * ctx->Nv, kind, ctx->stream), "copy v out"))
     return HERMITE_ERR_CUDA;
   if (!cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "download sync")) return HERMITE_ERR_CUDA;
-  return HERMITE_OK;
+  return tc_check_status(ctx);
 }
 
 // conservative start-up: dual level at dt/2 from the primal (u, v) data held
@@ -309,6 +314,7 @@ int create_context(int d, int m, int64_t N, double c, double h, double dt, int v
       if (!cuda_ok(ctx, cudaMemset(ctx->fgrid[g], 0, sizeof(float2) * ctx->ncoef * ctx->ld[g]), "memset"))
         rc = HERMITE_ERR_CUDA;
     if (rc == HERMITE_OK) rc = build_split_operator(ctx);
+    if (rc == HERMITE_OK) rc = build_tc_operator(ctx);
     if (rc == HERMITE_OK) rc = build_split_forms(ctx);
     if (cons) alloc((void **)&ctx->fscratch, sizeof(float2) * ctx->Nu * maxld, "split scratch");
   }

@@ -210,9 +210,13 @@ __global__ void reduce_kernel(const double *partials, int64_t n, double scale, d
   if (threadIdx.x == 0) *out = scale * red[0];
 }
 
+// The quadratic form `form` of levels A, B over the cells of geometry g: the
+// factored kernel (sums of squares, no cancellation) where the context has
+// the factors, else the dense per-class form.  Block partial sums go to
+// `partials` (at most partials_len doubles).
 template <int D>
 int launch_energy_d(hermite_ctx *ctx, const Geometry &g, int form, const double *A, const double *B,
-                    double *result_slot) {
+                    double *result_slot, double *partials, int64_t partials_len) {
   const int nq = ctx->nq[form];
   const size_t smem = sizeof(double) * ((size_t)nq * nq + (size_t)nq * kEThreads) + nq + 16;
   static thread_local int configured_dev = -1;
@@ -225,7 +229,7 @@ int launch_energy_d(hermite_ctx *ctx, const Geometry &g, int form, const double 
   }
   const int nclass = 1 << D;
   int64_t blocks = std::max<int64_t>(1, (g.nodes_dst + kEThreads - 1) / kEThreads);
-  blocks = std::min<int64_t>(blocks, ctx->partials_len / nclass);
+  blocks = std::min<int64_t>(blocks, partials_len / nclass);
   dim3 grid((unsigned)blocks, (unsigned)nclass);
   if (ctx->L[form]) {
     static thread_local int configured_f = -1;
@@ -242,17 +246,17 @@ int launch_energy_d(hermite_ctx *ctx, const Geometry &g, int form, const double 
     const size_t smem_f = sizeof(double) * ((size_t)rmax * nq + (A == B ? 1 : 2) * (size_t)kFTile * ld + kFTile) +
                           sizeof(int64_t) * kFTile * nclass + sizeof(int) * kFTile * nclass + 3 * nq + 16;
     int64_t fblocks = std::max<int64_t>(1, (g.nodes_dst + kFTile - 1) / kFTile);
-    fblocks = std::min<int64_t>(fblocks, ctx->partials_len / nclass);
+    fblocks = std::min<int64_t>(fblocks, partials_len / nclass);
     dim3 fgrid((unsigned)fblocks, (unsigned)nclass);
     energy_factored_kernel<D><<<fgrid, kFThreads, smem_f, ctx->stream>>>(
         g, ctx->L[form], ctx->lrows[form], rmax, ctx->ltri[form], ctx->lperm[form], nq, ctx->par_in, A, B,
-        ctx->partials);
-    reduce_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, fblocks * nclass, ctx->formscale[form], result_slot);
+        partials);
+    reduce_kernel<<<1, 256, 0, ctx->stream>>>(partials, fblocks * nclass, ctx->formscale[form], result_slot);
     return cuda_ok(ctx, cudaGetLastError(), "energy_factored_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
   } else {
-    energy_kernel<D><<<grid, kEThreads, smem, ctx->stream>>>(g, ctx->Q[form], nq, ctx->par_in, A, B, ctx->partials);
+    energy_kernel<D><<<grid, kEThreads, smem, ctx->stream>>>(g, ctx->Q[form], nq, ctx->par_in, A, B, partials);
   }
-  reduce_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, blocks * nclass, ctx->formscale[form], result_slot);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partials, blocks * nclass, ctx->formscale[form], result_slot);
   return cuda_ok(ctx, cudaGetLastError(), "energy_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
@@ -262,9 +266,9 @@ int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const
   // cells of a level held on grid g are centred at the nodes of grid 1-g
   const Geometry geo = make_geometry(ctx, 1 - g);
   switch (ctx->d) {
-    case 1: return launch_energy_d<1>(ctx, geo, form, A, B, result_slot);
-    case 2: return launch_energy_d<2>(ctx, geo, form, A, B, result_slot);
-    case 3: return launch_energy_d<3>(ctx, geo, form, A, B, result_slot);
+    case 1: return launch_energy_d<1>(ctx, geo, form, A, B, result_slot, ctx->partials, ctx->partials_len);
+    case 2: return launch_energy_d<2>(ctx, geo, form, A, B, result_slot, ctx->partials, ctx->partials_len);
+    case 3: return launch_energy_d<3>(ctx, geo, form, A, B, result_slot, ctx->partials, ctx->partials_len);
   }
   return HERMITE_ERR_ARG;
 }
@@ -301,27 +305,6 @@ double *noalloc_scratch(hermite_ctx *ctx, int dev) {
     g_noalloc_ptr[dev] = static_cast<double *>(p);
   }
   return g_noalloc_ptr[dev];
-}
-
-template <int D>
-int launch_energy_noalloc_d(hermite_ctx *ctx, const Geometry &g, int form, const double *A, double *partials,
-                            double *out) {
-  const int nq = ctx->nq[form];
-  const size_t smem = sizeof(double) * ((size_t)nq * nq + (size_t)nq * kEThreads) + nq + 16;
-  // the shared-memory opt-in is a host driver call: once per device and thread
-  static thread_local int configured_dev = -1;
-  if (configured_dev != ctx->device) {
-    if (!cuda_ok(ctx,
-                 cudaFuncSetAttribute(energy_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024),
-                 "cudaFuncSetAttribute energy"))
-      return HERMITE_ERR_CUDA;
-    configured_dev = ctx->device;
-  }
-  const int64_t blocks = std::max<int64_t>(1, (g.nodes_dst + kEThreads - 1) / kEThreads);
-  dim3 grid((unsigned)blocks, (unsigned)(1 << D));
-  energy_kernel<D><<<grid, kEThreads, smem, ctx->stream>>>(g, ctx->Q[form], nq, ctx->par_in, A, A, partials);
-  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partials, blocks * (1 << D), ctx->formscale[form], out);
-  return cuda_ok(ctx, cudaGetLastError(), "energy_kernel (no-alloc)") ? HERMITE_OK : HERMITE_ERR_CUDA;
 }
 
 }  // namespace
@@ -362,9 +345,9 @@ extern "C" int hermite_energy_noalloc(hermite_ctx *ctx, int grid, const double *
   for (int f = 0; f < kNumForms; ++f) {
     int rc;
     switch (ctx->d) {
-      case 1: rc = launch_energy_noalloc_d<1>(ctx, g, f, level, partials, out_dev + f); break;
-      case 2: rc = launch_energy_noalloc_d<2>(ctx, g, f, level, partials, out_dev + f); break;
-      default: rc = launch_energy_noalloc_d<3>(ctx, g, f, level, partials, out_dev + f); break;
+      case 1: rc = launch_energy_d<1>(ctx, g, f, level, level, out_dev + f, partials, kNoAllocPartials); break;
+      case 2: rc = launch_energy_d<2>(ctx, g, f, level, level, out_dev + f, partials, kNoAllocPartials); break;
+      default: rc = launch_energy_d<3>(ctx, g, f, level, level, out_dev + f, partials, kNoAllocPartials); break;
     }
     if (rc) return rc;
   }

@@ -77,6 +77,17 @@ struct hermite_ctx {
   int16_t *prow = nullptr;     // [2^d][pslots] output row of each slot (-1 unused)
   int8_t *pcls = nullptr;      // [2^d][2]
   int pslots = 0, psplit = 0;
+  // tensor-core split half-step (d >= 2, every parity class of inputs and of
+  // outputs at most 16 wide): the operator's BF16 digit image, the class
+  // tables and row exponents; split_engine 1 runs it, 0 the CUDA-core kernel
+  bool tc_ready = false;
+  int split_engine = 0;
+  int tc_vexp = 0;             // velocity inputs are scaled by 2^tc_vexp
+  uint4 *tc_B = nullptr;       // [group][input class][class in group][96 x 16 BF16]
+  int16_t *tc_inb = nullptr;   // [2^d][16]
+  int16_t *tc_orow = nullptr;  // [2^d][16]
+  int8_t *tc_er = nullptr;     // [nco]
+  int *tc_status = nullptr;    // bounded-wait error word
   // 1-D matrices of the sum-factorised dissipative energies (two class bits)
   double *tpm = nullptr;
   float2 *tpmf = nullptr;
@@ -108,6 +119,14 @@ int build_split_forms(hermite_ctx *ctx);
 int launch_energy_form_split(hermite_ctx *ctx, int form, int grid, const float2 *A, const float2 *B,
                              double *result_slot);
 int launch_half_step_split_into(hermite_ctx *ctx, int dst, const float2 *src, float2 *out, bool subtract_old);
+
+// Tensor-core split half-step (hermite_tc_step.cu).  build_tc_operator sets
+// tc_ready (and split_engine = 1) where the shapes allow; the launch writes
+// `out` from `src` like launch_half_step_split_into; tc_check_status returns
+// HERMITE_ERR_TIMEOUT (once) if a bounded wait of the kernel ran out.
+int build_tc_operator(hermite_ctx *ctx);
+int launch_half_step_tc(hermite_ctx *ctx, int dst, const float2 *src, float2 *out, bool subtract_old);
+int tc_check_status(hermite_ctx *ctx);
 
 // Energy reduction (hermite_energy.cu).
 int launch_energy_form(hermite_ctx *ctx, int form, int g, const double *A, const double *B,

@@ -604,6 +604,7 @@ int launch_energy_form_split(hermite_ctx *ctx, int form, int grid, const float2 
 }
 
 int launch_half_step_split_into(hermite_ctx *ctx, int dst, const float2 *src, float2 *out, bool subtract_old) {
+  if (ctx->tc_ready && ctx->split_engine == 1) return launch_half_step_tc(ctx, dst, src, out, subtract_old);
   const Geometry g = make_geometry(ctx, dst);
   switch (ctx->d) {
     case 1: return launch_split_d<1>(ctx, g, src, out, subtract_old);
@@ -617,6 +618,7 @@ int launch_half_step_split(hermite_ctx *ctx, int dst, bool subtract_old) {
   const Geometry g = make_geometry(ctx, dst);
   const float2 *src = ctx->fgrid[1 - dst];
   float2 *out = ctx->fgrid[dst];
+  if (ctx->tc_ready && ctx->split_engine == 1) return launch_half_step_tc(ctx, dst, src, out, subtract_old);
   switch (ctx->d) {
     case 1: return launch_split_d<1>(ctx, g, src, out, subtract_old);
     case 2: return launch_split_d<2>(ctx, g, src, out, subtract_old);

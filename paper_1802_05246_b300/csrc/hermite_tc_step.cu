@@ -1,0 +1,733 @@
+// Tensor-core (tcgen05) building blocks of the split-precision half-step.
+//
+// hermite_tc_selftest checks, on the device it runs on, the two properties the
+// tensor-core half-step rests on:
+//  * the shared-memory operand layout of tc::desc_kmajor (K-major, no swizzle,
+//    16-column tiles), B operands cut to their first N rows and accumulators
+//    placed at a column offset in tensor memory;
+//  * exact FP32 accumulation of products of integer-valued BF16 operands
+//    (|a|, |b| <= 256, K <= 128): every partial sum is an integer below 2^24.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hermite_device.cuh"
+
+#include "hermite_internal.h"
+#include "hermite_tc.cuh"
+
+namespace hermite {
+namespace {
+
+constexpr int kSelfMaxK = 128, kSelfMaxN = 96;
+
+__global__ void __launch_bounds__(128) tc_selftest_kernel(const float *__restrict__ A, const float *__restrict__ B,
+                                                          int K, int N, float *__restrict__ D0,
+                                                          float *__restrict__ D1, int *status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int nch = K / 16;
+  unsigned char *As = sm;                       // [chunk][4096 B]
+  unsigned char *Bs = As + nch * 4096;          // [chunk][N rows x 32 B]
+  uint64_t *bar = reinterpret_cast<uint64_t *>(Bs + nch * N * 32);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < 128 * K; i += 128) {
+    const int r = i / K, k = i % K;
+    *reinterpret_cast<__nv_bfloat16 *>(As + (k / 16) * 4096 + tc::kmajor16_offset(r, k % 16)) =
+        __float2bfloat16_rn(A[i]);
+  }
+  for (int i = tid; i < N * K; i += 128) {
+    const int r = i / K, k = i % K;
+    *reinterpret_cast<__nv_bfloat16 *>(Bs + (k / 16) * N * 32 + tc::kmajor16_offset(r, k % 16)) =
+        __float2bfloat16_rn(B[i]);
+  }
+  tc::fence_async_smem();
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  if (warp == 0) {
+    tc::alloc(slot, 256);
+    tc::relinquish();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *slot;
+  if (tid == 0) {
+    for (int ch = 0; ch < nch; ++ch) {
+      const uint64_t da = tc::desc_kmajor(As + ch * 4096, 128, 256);
+      const uint64_t db = tc::desc_kmajor(Bs + ch * N * 32, 128, 256);
+      // D0 = A B^T at columns [0, N); D1 = A B[0:N-16]^T at columns [128 + 16, 128 + N)
+      tc::mma(tmem, da, db, tc::idesc_bf16(128, N), ch > 0);
+      tc::mma(tmem + 128 + 16, da, db, tc::idesc_bf16(128, N - 16), ch > 0);
+    }
+    tc::commit(bar);
+  }
+  const bool ok = tc::mbar_wait(bar, 0);
+  tc::fence_after();
+  if (ok) {
+    const int row = tid;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      for (int j = 0; j < 16; ++j) D0[row * N + c0 + j] = v[j];
+    }
+    for (int c0 = 16; c0 < N; c0 += 16) {
+      float v[16];
+      tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + 128 + c0, v);
+      for (int j = 0; j < 16; ++j) D1[row * (N - 16) + c0 - 16 + j] = v[j];
+    }
+  } else if ((tid & 31) == 0) {
+    atomicExch(status, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, 256);
+}
+
+// deterministic integer test values in [-256, 256], mostly of full size with
+// some small ones; the sign is a row sign times a column sign shared by A and
+// B, so that every product of a row pair has the same sign and the sums come
+// close to 2^23 (exactness is tested near the top and at the bottom bit)
+uint32_t selftest_hash(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+float selftest_value(uint32_t row, uint32_t k, uint32_t salt) {
+  const uint32_t h = selftest_hash(row * 1315423911u + k * 2654435761u + salt * 97u);
+  const int sign = ((selftest_hash(row * 7919u + salt) ^ selftest_hash(k + 12345u)) & 1) ? -1 : 1;
+  const uint32_t kind = h % 8;
+  const int mag = kind < 6 ? 256 - (int)((h >> 4) % 3) : (int)((h >> 4) % 7) + 1;
+  return (float)(sign * mag);
+}
+
+}  // namespace
+}  // namespace hermite
+
+extern "C" int hermite_tc_selftest(int K, int N, float *A, float *B, float *D0, float *D1) {
+  using namespace hermite;
+  if (K < 16 || K > kSelfMaxK || K % 16 || N < 32 || N > kSelfMaxN || N % 16 || !A || !B || !D0 || !D1)
+    return HERMITE_ERR_ARG;
+  for (int i = 0; i < 128 * K; ++i) A[i] = selftest_value(i / K, i % K, 1);
+  for (int i = 0; i < N * K; ++i) B[i] = selftest_value(i / K, i % K, 2);
+  float *dA = nullptr;
+  const size_t nA = 128 * (size_t)K, nB = (size_t)N * K, n0 = 128 * (size_t)N, n1 = 128 * (size_t)(N - 16);
+  if (device_alloc(&dA, sizeof(float) * (nA + nB + n0 + n1) + 16) != cudaSuccess) return HERMITE_ERR_ALLOC;
+  float *dB = dA + nA, *dD0 = dB + nB, *dD1 = dD0 + n0;
+  int *dstatus = reinterpret_cast<int *>(dD1 + n1);
+  int status = 0, rc = HERMITE_OK;
+  const size_t smem = (size_t)(K / 16) * (4096 + N * 32) + 64;
+  if (cudaMemcpy(dA, A, sizeof(float) * nA, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dB, B, sizeof(float) * nB, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(dstatus, 0, sizeof(int)) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+    rc = HERMITE_ERR_CUDA;
+  } else {
+    tc_selftest_kernel<<<1, 128, smem>>>(dA, dB, K, N, dD0, dD1, dstatus);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(D0, dD0, sizeof(float) * n0, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(D1, dD1, sizeof(float) * n1, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = HERMITE_ERR_CUDA;
+    else if (status)
+      rc = HERMITE_ERR_TIMEOUT;
+  }
+  cudaFree(dA);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Split-precision half-step on the tensor cores.
+//
+// The map is the one of the CUDA-core kernels: corner gather with the ghost
+// signs of Sec. 3.1.3, Walsh-Hadamard transform over the 2^d corners
+// (z_q[b] = sum_s (-1)^{|q & s|} x_s[b]) and, for every output a of parity
+// class c = par(a), out[a] = sum_b M0[a][b] Y_c[b] with Y_c[b] = z_{c ^ par(b)}[b].
+// Per output class this is a product (nodes x inputs) . (inputs x outputs),
+// done here on tcgen05 with an exact digit split (the fixed-point slicing of
+// Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication", 2012):
+//  * data side: per node and class, Y_c scaled by 2^(8 - E_c), with 2^E_c
+//    above max |Y_c| (a bound from an FP32 pre-pass), split into six signed
+//    8-bit digits A_0..A_5 (|A_0| <= 256, the rest <= 128, each exact in BF16);
+//  * operator side: M' = M0 with its velocity columns divided by 2^vexp (the
+//    data side multiplies velocity inputs by 2^vexp, which balances u and v),
+//    each row scaled by 2^(8 - er[a]) and split into seven digits B_0..B_6;
+//  * every product A_i . B_j with i + j <= 6 is formed by tcgen05.mma in FP32:
+//    all terms are integers and every partial sum stays below 2^24 (at most
+//    91 inputs), so each is exact; the products of one diagonal k = i + j
+//    share an accumulator, seven diagonals per class in tensor memory;
+//  * out[a] = 2^(E_c + er[a] - 16) sum_k 2^(-8k) D_k[a], summed in FP32 hi + lo.
+// What is dropped: data digits below 2^-48 of the class maximum and the digit
+// products below 2^-56 of the row and class maxima.
+//
+// Work split: a CTA owns 128 consecutive target nodes at a time (one per
+// tensor-memory lane); 256 threads, thread t and t + 128 share a node and
+// take the first and the second 8 inputs of each 16-input parity class.
+// Per tile, one FP32 pre-pass over the corner data bounds max |Y_c| for all
+// classes.  Output classes then go in groups of four (3-D: two groups), so
+// that a group's accumulators (4 classes x 7 diagonals x 16 columns) fit in
+// tensor memory.  Per input parity class p (a 16-wide K chunk, whose inputs
+// share their parity and so their ghost signs), the threads write the digits
+// of their inputs to one of two shared-memory A buffers while the tensor core
+// works on the other; thread 0 issues 24 MMAs (4 classes x 6 data digits,
+// N = 16 (7 - i) operator digits each) and commits them to the buffer's
+// mbarrier; the epilogue reads the diagonals with tcgen05.ld.
+// ---------------------------------------------------------------------------
+namespace hermite {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcDigits = 6;                         // data digits
+constexpr int kTcMDigits = 7;                        // operator digits = diagonals
+constexpr int kTcClasses = 4;                        // output classes per group
+constexpr int kTcCols = kTcMDigits * 16;             // tensor-memory columns per class
+constexpr int kTcTileA = 4096;                       // 128 rows x 16 K, BF16
+constexpr int kTcTileB = kTcCols * 32;               // 112 rows x 16 K, BF16
+constexpr int kTcBufA = kTcClasses * kTcDigits * kTcTileA;
+constexpr int kTcBufB = kTcClasses * kTcTileB;
+constexpr int kTcMaxNC = 8;
+constexpr size_t kTcSmem = 2 * (size_t)kTcBufA + 2 * (size_t)kTcBufB + kTcMaxNC * 128 * 4 + 4 * kTcMaxNC * 16 + 64;
+
+struct TcArgs {
+  Geometry g;
+  const float2 *src;
+  float2 *dst;
+  int subtract_old;
+  const uint4 *Bimg;     // [group][input class][class in group][112 x 16 K-major BF16 tile]
+  const int16_t *inb;    // [2^d][16] input coefficient at (input class, position), -1 = none
+  const int16_t *orow;   // [2^d][16] output row at (output class, position), -1 = none
+  const int8_t *er;      // [nco] operator row exponents
+  int nu;                // inputs b >= nu are velocity coefficients
+  int vexp;              // velocity inputs are multiplied by 2^vexp
+  int *status;           // set by a bounded wait that ran out
+};
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }  // e in [-126, 127]
+
+// 2^e for e in [-252, 252] as a product of two normal powers of two
+__device__ __forceinline__ float2 pow2_split(int e) {
+  const int e1 = e / 2;
+  return make_float2(pow2f(e1), pow2f(e - e1));
+}
+
+// FP32 transform over all 2^d corners (butterflies in the order of the
+// corner bits): z[q] = sum_s (-1)^{|q & s|} x[s]
+template <int D>
+__device__ __forceinline__ void transform_f32(float *x) {
+#pragma unroll
+  for (int bm = 1; bm < (1 << D); bm <<= 1)
+#pragma unroll
+    for (int i = 0; i < (1 << D); ++i)
+      if (!(i & bm)) {
+        const float a = x[i], c = x[i | bm];
+        x[i] = __fadd_rn(a, c);
+        x[i | bm] = __fsub_rn(a, c);
+      }
+}
+
+// FP32 hi + lo sums of packed pairs: (a.x + b.x, a.y + b.y) for two
+// independent values given as hi and lo pairs (Knuth's two-sum on packed
+// operands, then the lo parts added to the error)
+__device__ __forceinline__ void df_add_x2(float2 &ah, float2 &al, const float2 bh, const float2 bl) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 s = __fadd2_rn(ah, bh);
+  const float2 bb = __ffma2_rn(ah, m1, s);                 // s - a
+  const float2 t1 = __ffma2_rn(bb, m1, s);                 // s - bb
+  const float2 e1 = __ffma2_rn(t1, m1, ah);                // a - (s - bb)
+  const float2 e2 = __ffma2_rn(bb, m1, bh);                // b - bb
+  const float2 e = __fadd2_rn(__fadd2_rn(e1, e2), __fadd2_rn(al, bl));
+  ah = s;
+  al = e;
+}
+
+// Corner transform restricted to one group of four output classes, in
+// FP32 hi + lo on packed pairs: the values z_q for q = (4 g + cc) ^ p,
+// cc = 0..3, of corner data (xh, xl) with ghost signs applied.  3-D: the top
+// corner bit of q is fixed by the group; 2-D: the full 4-point transform.
+template <int D>
+__device__ __forceinline__ void group_transform_x2(const float *xh, const float *xl, int gi, int p, float2 *out) {
+  float yh[4], yl[4];
+  if constexpr (D == 3) {
+    const float sg = ((gi ^ (p >> 2)) & 1) ? -1.0f : 1.0f;
+    float2 ah0 = make_float2(xh[0], xh[1]), al0 = make_float2(xl[0], xl[1]);
+    float2 ah1 = make_float2(xh[2], xh[3]), al1 = make_float2(xl[2], xl[3]);
+    df_add_x2(ah0, al0, make_float2(sg * xh[4], sg * xh[5]), make_float2(sg * xl[4], sg * xl[5]));
+    df_add_x2(ah1, al1, make_float2(sg * xh[6], sg * xh[7]), make_float2(sg * xl[6], sg * xl[7]));
+    yh[0] = ah0.x; yh[1] = ah0.y; yh[2] = ah1.x; yh[3] = ah1.y;
+    yl[0] = al0.x; yl[1] = al0.y; yl[2] = al1.x; yl[3] = al1.y;
+  } else {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      yh[s] = xh[s];
+      yl[s] = xl[s];
+    }
+  }
+  // level over corner bit 0: (y0 + y1, y2 + y3) and (y0 - y1, y2 - y3)
+  float2 sh = make_float2(yh[0], yh[2]), sl = make_float2(yl[0], yl[2]);
+  float2 dh = sh, dl = sl;
+  df_add_x2(sh, sl, make_float2(yh[1], yh[3]), make_float2(yl[1], yl[3]));
+  df_add_x2(dh, dl, make_float2(-yh[1], -yh[3]), make_float2(-yl[1], -yl[3]));
+  // level over corner bit 1: q = 0: a0 + a2, 1: a1 + a3, 2: a0 - a2, 3: a1 - a3
+  float2 ph = make_float2(sh.x, dh.x), pl = make_float2(sl.x, dl.x);  // (a0, a1)
+  float2 mh = ph, ml = pl;
+  df_add_x2(ph, pl, make_float2(sh.y, dh.y), make_float2(sl.y, dl.y));    // (z0, z1)
+  df_add_x2(mh, ml, make_float2(-sh.y, -dh.y), make_float2(-sl.y, -dl.y));  // (z2, z3)
+  float2 zq[4] = {make_float2(ph.x, pl.x), make_float2(ph.y, pl.y), make_float2(mh.x, ml.x), make_float2(mh.y, ml.y)};
+#pragma unroll
+  for (int cc = 0; cc < 4; ++cc) out[cc] = zq[(cc ^ p) & 3];
+}
+
+// Six signed 8-bit digits of two values at once (a packed pair: u = value of
+// one class, w = another), each v = (hi + lo) * sc with |v| <= 256:
+// v = sum_i d_i 2^(-8 i) up to a remainder below 2^-41.  Each digit is the
+// nearest integer to the rounded sum of the remainder pair (1.5 * 2^23 shift),
+// the remainder itself is kept exactly as hi and lo parts, so |d_0| <= 256 and
+// |d_i| <= 128 for i > 0 (every digit exact in BF16).
+__device__ __forceinline__ void six_digits2(float2 u, float2 w, float sc_u, float sc_w, float (&du)[kTcDigits],
+                                            float (&dw)[kTcDigits]) {
+  const float2 C = make_float2(12582912.0f, 12582912.0f), S = make_float2(256.0f, 256.0f);
+  const float2 M1 = make_float2(-1.0f, -1.0f);
+  float2 rh = make_float2(__fmul_rn(u.x, sc_u), __fmul_rn(w.x, sc_w));
+  float2 rl = make_float2(__fmul_rn(u.y, sc_u), __fmul_rn(w.y, sc_w));
+#pragma unroll
+  for (int i = 0; i < kTcDigits; ++i) {
+    if (i > 0) {
+      rh = __fmul2_rn(rh, S);
+      rl = __fmul2_rn(rl, S);
+    }
+    // u - v is formed as fma(v, -1, u), which rounds like the subtraction
+    const float2 q = __ffma2_rn(C, M1, __fadd2_rn(__fadd2_rn(rh, rl), C));
+    rh = __ffma2_rn(q, M1, rh);
+    du[i] = q.x;
+    dw[i] = q.y;
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&b);
+}
+
+// smallest E with 2^E > m (m >= 0), clamped to the range the scalings use
+__device__ __forceinline__ int bound_exponent(float m) {
+  if (!(m > 0.0f)) return -100;
+  const int e = ((__float_as_int(m) >> 23) & 0xFF) - 127;
+  return max(-100, min(100, e + 1));
+}
+
+}  // namespace
+}  // namespace hermite
+
+namespace hermite {
+namespace {
+
+template <int D>
+__global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArgs a) {
+  constexpr int NC = 1 << D;
+  constexpr int NG = NC / kTcClasses;  // groups of four output classes
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char *Abuf = tsm;                                           // [2][class][digit][4096]
+  unsigned char *Bbuf = Abuf + 2 * kTcBufA;                            // [2][class][112 x 16]
+  float *mxs = reinterpret_cast<float *>(Bbuf + 2 * kTcBufB);          // [class][128]
+  int16_t *s_inb = reinterpret_cast<int16_t *>(mxs + kTcMaxNC * 128);  // [NC][16]
+  int8_t *s_sh = reinterpret_cast<int8_t *>(s_inb + kTcMaxNC * 16);    // [NC][16]
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s_sh + 2 * kTcMaxNC * 16);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int node = tid & 127, half = tid >> 7;
+  const Geometry &g = a.g;
+  for (int i = tid; i < NC * 16; i += kTcThreads) {
+    const int b = a.inb[i];
+    s_inb[i] = (int16_t)b;
+    s_sh[i] = (int8_t)(b >= a.nu ? a.vexp : 0);
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::mbar_fence_init();
+  }
+  if (warp == 0) {
+    tc::alloc(slot, 512);
+    tc::relinquish();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  uint32_t it = 0;  // K chunks whose MMAs this CTA has issued
+  bool failed = false;
+  const int64_t ntiles = (g.nodes_dst + 127) / 128;
+  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int64_t t = tile * 128 + node;
+    const bool valid = t < g.nodes_dst;
+    int idx[NC];
+    uint64_t negm = 0;  // byte p: corners whose ghost image flips inputs of parity p
+    {
+      int64_t li[NC];
+      int gm[NC];
+      if (valid) {
+        dev::cell_corners<D>(g, t, li, gm);
+      } else {
+#pragma unroll
+        for (int s = 0; s < NC; ++s) {
+          li[s] = 0;
+          gm[s] = 0;
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        idx[s] = (int)li[s];
+        if (gm[s])
+#pragma unroll
+          for (int p = 0; p < NC; ++p)
+            if (dev::ghost_negates(g.bc, gm[s], p)) negm |= (uint64_t)1 << (8 * p + s);
+      }
+    }
+    // ---- pre-pass: bound max |Y_c| for every output class (FP32 transform of
+    // the hi parts; the lo parts and the roundings are covered by 2^-20 sum |x|)
+    float mx[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) mx[c] = 0.f;
+#pragma unroll
+    for (int p = 0; p < NC; ++p) {
+      const uint32_t neg = (uint32_t)(negm >> (8 * p)) & 0xFF;
+      for (int kk = 0; kk < 8; ++kk) {
+        const int b = s_inb[p * 16 + half * 8 + kk];
+        if (b < 0) break;  // a class's inputs come first, the padding after
+        const float2 *plane = a.src + (size_t)b * g.ld_src;
+        float x[NC], S = 0.f;
+#pragma unroll
+        for (int s = 0; s < NC; ++s) {
+          float v = valid ? plane[idx[s]].x : 0.f;
+          if ((neg >> s) & 1) v = -v;
+          x[s] = v;
+          S += fabsf(v);
+        }
+        transform_f32<D>(x);
+        const float sc = pow2f(s_sh[p * 16 + half * 8 + kk]), slack = S * 9.5367431640625e-07f;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) mx[q ^ p] = fmaxf(mx[q ^ p], (fabsf(x[q]) + slack) * sc);
+      }
+    }
+    // combine the two halves of each node's inputs
+    if (half) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) mxs[c * 128 + node] = mx[c];
+    }
+    __syncthreads();
+    if (!half) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        mx[c] = fmaxf(mx[c], mxs[c * 128 + node]);
+        mxs[c * 128 + node] = mx[c];
+      }
+    }
+    __syncthreads();
+    int E[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) E[c] = bound_exponent(mxs[c * 128 + node]);
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) {
+      if (failed) break;
+      // per-class digit scales of u and (balanced) v inputs
+      float scu[kTcClasses], scv[kTcClasses];
+#pragma unroll
+      for (int cc = 0; cc < kTcClasses; ++cc) {
+        scu[cc] = pow2f(8 - E[gi * kTcClasses + cc]);
+        scv[cc] = pow2f(a.vexp + 8 - E[gi * kTcClasses + cc]);
+      }
+      // ---- K loop over input parity classes
+      for (int p = 0; p < NC; ++p, ++it) {
+        const int buf = it & 1;
+        if (it >= 2) {
+          const bool ok = tc::mbar_wait(&bar[buf], ((it >> 1) - 1) & 1);
+          if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+          }
+        }
+        const uint4 *bsrc = a.Bimg + (size_t)(gi * NC + p) * (kTcBufB / 16);
+        uint4 *bdst = reinterpret_cast<uint4 *>(Bbuf + buf * kTcBufB);
+        for (int i = tid; i < kTcBufB / 16; i += kTcThreads) bdst[i] = bsrc[i];
+        const uint32_t neg = (uint32_t)(negm >> (8 * p)) & 0xFF;
+        uint32_t pk[kTcClasses][kTcDigits][4];
+        float dprev[kTcClasses][kTcDigits];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const int b = s_inb[p * 16 + half * 8 + kk];
+          float xh[NC], xl[NC];
+          const float2 *plane = a.src + (size_t)max(b, 0) * g.ld_src;
+#pragma unroll
+          for (int s = 0; s < NC; ++s) {
+            float2 v = (valid && b >= 0) ? plane[idx[s]] : make_float2(0.f, 0.f);
+            if ((neg >> s) & 1) v = make_float2(-v.x, -v.y);
+            xh[s] = v.x;
+            xl[s] = v.y;
+          }
+          float2 z[4];
+          group_transform_x2<D>(xh, xl, gi, p, z);
+          const bool isv = s_sh[p * 16 + half * 8 + kk] != 0;
+          float d[kTcClasses][kTcDigits];
+          six_digits2(z[0], z[1], isv ? scv[0] : scu[0], isv ? scv[1] : scu[1], d[0], d[1]);
+          six_digits2(z[2], z[3], isv ? scv[2] : scu[2], isv ? scv[3] : scu[3], d[2], d[3]);
+#pragma unroll
+          for (int cc = 0; cc < kTcClasses; ++cc)
+#pragma unroll
+            for (int i = 0; i < kTcDigits; ++i) {
+              if (kk & 1)
+                pk[cc][i][kk >> 1] = pack_bf16x2(dprev[cc][i], d[cc][i]);
+              else
+                dprev[cc][i] = d[cc][i];
+            }
+        }
+        unsigned char *Ab = Abuf + buf * kTcBufA + tc::kmajor16_offset(node, half * 8);
+#pragma unroll
+        for (int cc = 0; cc < kTcClasses; ++cc)
+#pragma unroll
+          for (int i = 0; i < kTcDigits; ++i)
+            *reinterpret_cast<uint4 *>(Ab + (cc * kTcDigits + i) * kTcTileA) =
+                make_uint4(pk[cc][i][0], pk[cc][i][1], pk[cc][i][2], pk[cc][i][3]);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after();
+#pragma unroll
+          for (int cc = 0; cc < kTcClasses; ++cc) {
+            const uint64_t db = tc::desc_kmajor(Bbuf + buf * kTcBufB + cc * kTcTileB, 128, 256);
+#pragma unroll
+            for (int i = 0; i < kTcDigits; ++i) {
+              const uint64_t da = tc::desc_kmajor(Abuf + buf * kTcBufA + (cc * kTcDigits + i) * kTcTileA, 128, 256);
+              tc::mma(tmem + cc * kTcCols + 16 * i, da, db, tc::idesc_bf16(128, 16 * (kTcMDigits - i)),
+                      (p > 0 || i > 0) ? 1u : 0u);
+            }
+          }
+          tc::commit(&bar[buf]);
+        }
+      }
+      if (failed) break;
+      // ---- epilogue: the seven diagonals of each class -> FP32 hi + lo outputs
+      {
+        const uint32_t last = it - 1;
+        const bool ok = tc::mbar_wait(&bar[last & 1], (last >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          break;
+        }
+      }
+      tc::fence_after();
+#pragma unroll
+      for (int cq = 0; cq < 2; ++cq) {
+        const int cc = half * 2 + cq, c = gi * kTcClasses + cc;
+        const int Ec = half ? E[gi * kTcClasses + 2 + cq] : E[gi * kTcClasses + cq];
+        float acc[kTcMDigits][16];
+#pragma unroll
+        for (int k = 0; k < kTcMDigits; ++k) tc::ld16(tmem + lane_base + cc * kTcCols + 16 * k, acc[k]);
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+          const int row = a.orow[c * 16 + n];
+          if (row < 0) continue;
+          float2 r = make_float2(acc[kTcMDigits - 1][n] * pow2f(-8 * (kTcMDigits - 1)), 0.f);
+#pragma unroll
+          for (int k = kTcMDigits - 2; k >= 0; --k) r = dev::df_add(r, make_float2(acc[k][n] * pow2f(-8 * k), 0.f));
+          const float2 sc = pow2_split(Ec + a.er[row] - 16);
+          r = make_float2(__fmul_rn(__fmul_rn(r.x, sc.x), sc.y), __fmul_rn(__fmul_rn(r.y, sc.x), sc.y));
+          if (valid) {
+            float2 *o = a.dst + (size_t)row * g.ld_dst + t;
+            if (a.subtract_old) r = dev::df_add(r, dev::df_neg(*o));
+            *o = dev::df_norm(r);
+          }
+        }
+      }
+      tc::fence_before();
+      __syncthreads();  // tensor memory read before the next group's first MMA overwrites it
+    }
+  }
+  if (failed) {
+    // let the MMAs still in flight finish (bounded) before the memory goes
+    if (it > 0) (void)tc::mbar_wait(&bar[(it - 1) & 1], ((it - 1) >> 1) & 1);
+    if (tid == 0) atomicExch(a.status, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, 512);
+}
+
+}  // namespace
+}  // namespace hermite
+
+namespace hermite {
+
+// Host side of the tensor-core half-step: the operator's digit image.
+// M' = M0 with velocity columns divided by 2^vexp; row a scaled by
+// 2^(8 - er[a]) (2^er[a] > max_b |M'[a][b]|) and split, in FP64 (exact), into
+// seven digits by rounding to the nearest integer, remainder times 256.  Tile
+// (group, input class p, class cc of the group) holds rows j * 16 + n (digit
+// j of output n of class 4 group + cc) and K columns k (input k of class p),
+// zero where a class has fewer than 16 members.
+int build_tc_operator(hermite_ctx *ctx) {
+  ctx->tc_ready = false;
+  ctx->split_engine = 0;
+  const int d = ctx->d, NC = 1 << d;
+  // every partial sum of a diagonal stays below 2^24 for at most 127 inputs;
+  // node indices and planes are addressed with 32-bit offsets
+  if (d < 2 || ctx->nci > 127 || ctx->nodes[0] >= (int64_t(1) << 31) || ctx->nodes[1] >= (int64_t(1) << 31))
+    return HERMITE_OK;
+  std::vector<double> M((size_t)ctx->nco * ctx->nci);
+  std::vector<int8_t> par(ctx->nci);
+  if (!cuda_ok(ctx, cudaMemcpy(M.data(), ctx->M, sizeof(double) * M.size(), cudaMemcpyDeviceToHost), "copy M") ||
+      !cuda_ok(ctx, cudaMemcpy(par.data(), ctx->par_in, par.size(), cudaMemcpyDeviceToHost), "copy parity"))
+    return HERMITE_ERR_CUDA;
+  std::vector<std::vector<int>> in_cls(NC), out_cls(NC);
+  for (int b = 0; b < ctx->nci; ++b) in_cls[par[b]].push_back(b);
+  for (int a = 0; a < ctx->nco; ++a) out_cls[par[a]].push_back(a);
+  for (int c = 0; c < NC; ++c)
+    if (in_cls[c].size() > 16 || out_cls[c].size() > 16) return HERMITE_OK;  // CUDA-core kernel only
+  const bool has_v = ctx->variant != HERMITE_CONSERVATIVE && ctx->Nv > 0;
+  const int vexp = has_v ? std::max(-15, std::min(15, (int)std::lround(std::log2(ctx->h / ctx->c)))) : 0;
+  std::vector<int8_t> er(ctx->nco, 0);
+  std::vector<double> Mp(M.size());
+  for (int a = 0; a < ctx->nco; ++a) {
+    double mx = 0.0;
+    for (int b = 0; b < ctx->nci; ++b) {
+      const double v = M[(size_t)a * ctx->nci + b] * (b >= ctx->Nu ? std::ldexp(1.0, -vexp) : 1.0);
+      Mp[(size_t)a * ctx->nci + b] = v;
+      mx = std::max(mx, std::fabs(v));
+    }
+    int e = 0;
+    if (mx > 0) std::frexp(mx, &e);  // mx < 2^e
+    if (e < -60 || e > 60) return HERMITE_OK;
+    er[a] = (int8_t)e;
+  }
+  const int NG = NC / 4;
+  const size_t tile_bytes = kTcTileB;
+  std::vector<uint16_t> img((size_t)NG * NC * 4 * tile_bytes / 2, 0);
+  for (int gi = 0; gi < NG; ++gi)
+    for (int p = 0; p < NC; ++p)
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = gi * 4 + cc;
+        uint16_t *tile = img.data() + ((size_t)(gi * NC + p) * 4 + cc) * (tile_bytes / 2);
+        for (size_t n = 0; n < out_cls[c].size(); ++n)
+          for (size_t k = 0; k < in_cls[p].size(); ++k) {
+            const int a = out_cls[c][n], b = in_cls[p][k];
+            double r = std::ldexp(Mp[(size_t)a * ctx->nci + b], 8 - er[a]);
+            for (int j = 0; j < kTcMDigits; ++j) {
+              const double dg = std::nearbyint(r);
+              r = (r - dg) * 256.0;
+              const float f = (float)dg;  // an integer of at most 9 bits: its BF16 is the top half
+              uint32_t bits;
+              std::memcpy(&bits, &f, 4);
+              tile[tc::kmajor16_offset(j * 16 + (int)n, (int)k) / 2] = (uint16_t)(bits >> 16);
+            }
+          }
+      }
+  std::vector<int16_t> inb((size_t)NC * 16, -1), orow((size_t)NC * 16, -1);
+  for (int c = 0; c < NC; ++c) {
+    for (size_t k = 0; k < in_cls[c].size(); ++k) inb[c * 16 + k] = (int16_t)in_cls[c][k];
+    for (size_t n = 0; n < out_cls[c].size(); ++n) orow[c * 16 + n] = (int16_t)out_cls[c][n];
+  }
+  if (!cuda_ok(ctx, device_alloc(&ctx->tc_B, img.size() * 2), "cudaMalloc tc_B") ||
+      !cuda_ok(ctx, device_alloc(&ctx->tc_inb, inb.size() * 2), "cudaMalloc tc_inb") ||
+      !cuda_ok(ctx, device_alloc(&ctx->tc_orow, orow.size() * 2), "cudaMalloc tc_orow") ||
+      !cuda_ok(ctx, device_alloc(&ctx->tc_er, er.size()), "cudaMalloc tc_er") ||
+      !cuda_ok(ctx, device_alloc(&ctx->tc_status, sizeof(int)), "cudaMalloc tc_status"))
+    return HERMITE_ERR_ALLOC;
+  if (!cuda_ok(ctx, cudaMemcpy(ctx->tc_B, img.data(), img.size() * 2, cudaMemcpyHostToDevice), "copy tc_B") ||
+      !cuda_ok(ctx, cudaMemcpy(ctx->tc_inb, inb.data(), inb.size() * 2, cudaMemcpyHostToDevice), "copy inb") ||
+      !cuda_ok(ctx, cudaMemcpy(ctx->tc_orow, orow.data(), orow.size() * 2, cudaMemcpyHostToDevice), "copy orow") ||
+      !cuda_ok(ctx, cudaMemcpy(ctx->tc_er, er.data(), er.size(), cudaMemcpyHostToDevice), "copy er") ||
+      !cuda_ok(ctx, cudaMemset(ctx->tc_status, 0, sizeof(int)), "clear tc_status"))
+    return HERMITE_ERR_CUDA;
+  ctx->tc_vexp = vexp;
+  ctx->tc_ready = true;
+  return HERMITE_OK;
+}
+
+namespace {
+template <int D>
+int launch_tc_d(hermite_ctx *ctx, const TcArgs &a) {
+  static thread_local int configured_dev = -1;
+  if (configured_dev != ctx->device) {
+    if (!cuda_ok(ctx, cudaFuncSetAttribute(half_step_tc_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kTcSmem),
+                 "cudaFuncSetAttribute tc"))
+      return HERMITE_ERR_CUDA;
+    configured_dev = ctx->device;
+  }
+  static thread_local int sms = 0, sms_dev = -1;
+  if (sms_dev != ctx->device) {
+    if (!cuda_ok(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "SM count"))
+      return HERMITE_ERR_CUDA;
+    sms_dev = ctx->device;
+  }
+  const int64_t ntiles = (a.g.nodes_dst + 127) / 128;
+  const int blocks = (int)std::min<int64_t>(ntiles, sms);
+  half_step_tc_kernel<D><<<blocks, kTcThreads, kTcSmem, ctx->stream>>>(a);
+  return cuda_ok(ctx, cudaGetLastError(), "half_step_tc_kernel") ? HERMITE_OK : HERMITE_ERR_CUDA;
+}
+}  // namespace
+
+int launch_half_step_tc(hermite_ctx *ctx, int dst, const float2 *src, float2 *out, bool subtract_old) {
+  TcArgs a;
+  a.g = make_geometry(ctx, dst);
+  if (a.g.nodes_dst == 0) return HERMITE_OK;
+  a.src = src;
+  a.dst = out;
+  a.subtract_old = subtract_old ? 1 : 0;
+  a.Bimg = ctx->tc_B;
+  a.inb = ctx->tc_inb;
+  a.orow = ctx->tc_orow;
+  a.er = ctx->tc_er;
+  a.nu = ctx->Nu;
+  a.vexp = ctx->tc_vexp;
+  a.status = ctx->tc_status;
+  switch (ctx->d) {
+    case 2: return launch_tc_d<2>(ctx, a);
+    case 3: return launch_tc_d<3>(ctx, a);
+  }
+  return HERMITE_ERR_ARG;
+}
+
+int tc_check_status(hermite_ctx *ctx) {
+  if (!ctx->tc_status) return HERMITE_OK;
+  int st = 0;
+  if (!cuda_ok(ctx, cudaMemcpy(&st, ctx->tc_status, sizeof(int), cudaMemcpyDeviceToHost), "read tc status"))
+    return HERMITE_ERR_CUDA;
+  if (st == 0) return HERMITE_OK;
+  cudaMemset(ctx->tc_status, 0, sizeof(int));
+  ctx->err = "tensor-core half-step: a bounded wait for the tensor core ran out";
+  return HERMITE_ERR_TIMEOUT;
+}
+
+}  // namespace hermite
+
+extern "C" int hermite_set_split_engine(hermite_ctx *ctx, int engine) {
+  using namespace hermite;
+  if (!ctx || (engine != 0 && engine != 1)) return HERMITE_ERR_ARG;
+  if (ctx->precision != HERMITE_SPLIT32) {
+    ctx->err = "hermite_set_split_engine: not a split-precision context";
+    return HERMITE_ERR_STATE;
+  }
+  if (engine == 1 && !ctx->tc_ready) {
+    ctx->err = "hermite_set_split_engine: no tensor-core kernel for this shape (d = 1 or a parity class wider than 16)";
+    return HERMITE_ERR_UNSUPPORTED;
+  }
+  ctx->split_engine = engine;
+  return HERMITE_OK;
+}
+
+extern "C" int hermite_get_split_engine(const hermite_ctx *ctx) {
+  if (!ctx || ctx->precision != HERMITE_SPLIT32) return -1;
+  return ctx->split_engine;
+}

@@ -94,13 +94,16 @@ def test_l2_error_matches_oracle(hb, orc, d, m, N, variant, bc, prec):
     g.close()
 
 
-def pulse_errors(hb, N, precision, nsteps=200, m=3, lam=0.9, variant=0):
-    """Relative L2 error of the 3-D pulse workload after nsteps full steps."""
+def pulse_errors(hb, N, precision, nsteps=200, m=3, lam=0.9, variant=0, engine=None):
+    """Relative L2 error of the 3-D pulse workload after nsteps full steps
+    (engine: the split engine to use, None for the default)."""
     import torch
 
     h = 1.0 / N
     cen, wid, amp = I.pulses_3d_config(0)
     g = hb.Hermite(3, m, N, 1.0, h, lam * h, variant, 0, precision=precision)
+    if engine is not None:
+        g.set_split_engine(engine)
     u0 = I.gaussian_data(3, m, N, h, I.PERIODIC, 0, cen, wid, amp)
     g.set_state(u0, np.zeros((N**3, m**3)) if variant != 1 else None)
     g.step(nsteps)

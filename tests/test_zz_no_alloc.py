@@ -55,6 +55,10 @@ def test_noalloc_energy_matches_hermite_energy(hb, orc, d, m, N, variant, bc):
         g.get_grid_device(grid, du, dv)
         level = _coef_major(du, dv)
         out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+        # beyond the sum-factorised range this entry point evaluates the dense
+        # per-class forms where hermite_energy uses their Cholesky factors: the
+        # two roundings differ by ~eps times the forms' condition
+        rtol = RTOL if m <= 8 else 1e-10
         for _call in range(2):  # two calls in a row share the library's array
             out.fill_(float("nan"))
             g.energy_noalloc(grid, level, nodes, out)
@@ -64,14 +68,14 @@ def test_noalloc_energy_matches_hermite_energy(hb, orc, d, m, N, variant, bc):
                 # the second form is c^2 int |grad p|^2 of the primal level;
                 # the first, the seminorm |p|^2_{m+1,..,m+1} of Sec. 4.2, is
                 # pinned to the oracle's quadrature of the same level
-                np.testing.assert_allclose(got[1], ref[0], rtol=RTOL)
+                np.testing.assert_allclose(got[1], ref[0], rtol=rtol)
                 lev = du.cpu().numpy()
                 # the oracle interpolates by LU of the confluent Vandermonde
                 # system: its forward error grows with that system's condition
                 otol = max(1e-10, 20 * np.finfo(float).eps * hermite_cond(m))
                 np.testing.assert_allclose(got[0], P.cons_forms(grid, lev, lev)[0], rtol=otol)
             else:
-                np.testing.assert_allclose(got, ref[:2], rtol=RTOL)
+                np.testing.assert_allclose(got, ref[:2], rtol=rtol)
         g.advance_half(1)
     g.close()
 
