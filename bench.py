@@ -68,6 +68,10 @@ ALG_BYTES_PER_LAUNCH = 2 * DOF_PER_HALF * 8
 # 64^3, scaled to 128^3 by the node count
 TRAFFIC_PER_LAUNCH = 373.8e6 * 8
 SPLIT_TRAFFIC_PER_LAUNCH = 362.3e6 * 8
+# tensor-core flops of the digit-split engine per node: 8 output classes x 8
+# input classes (K = 16 each) x sum over the six data digits i of N = 16 (7 - i)
+# operator-digit columns, two flops per multiply-add
+TC_FLOP_PER_NODE = 2 * (1 << D) * (1 << D) * 16 * sum(16 * (7 - i) for i in range(6))
 # FP32 operations the compensated (hi + lo) arithmetic spends per node: 12 per
 # multiply-add of an operator row, 8 per addition of the corner transform
 SPLIT_OPS_PER_NODE = (NU + NV) * (NU + NV) * 12 + (NU + NV) * D * (1 << D) * 8
@@ -267,10 +271,13 @@ def run_reference(args):
     return 0
 
 
-def measure(hb, torch, dev, u0, v0, precision, args, ws, want_clocks):
-    """Time W warm-up and K benchmark steps of one context; returns a dict."""
+def measure(hb, torch, dev, u0, v0, precision, args, ws, want_clocks, engine=None):
+    """Time W warm-up and K benchmark steps of one context; returns a dict
+    (engine: the split-precision engine, None for the default)."""
     h = 1.0 / N
     g = hb.Hermite(D, M, N, 1.0, h, LAM * h, hb.DISSIPATIVE, hb.PERIODIC, precision=precision)
+    if engine is not None:
+        g.set_split_engine(engine)
     stream = torch.cuda.Stream(device=dev)
     g.set_stream(stream)
     du = torch.from_numpy(u0).to(dev)
@@ -321,7 +328,7 @@ ACC_STEPS = 200      # full steps of the 3-D pulse workload
 ACC_CELLS = 2048     # cells sampled for the L2 errors (the same cells for every arithmetic)
 
 
-def accuracy(hb, torch, dev, u0, v0, precision):
+def accuracy(hb, torch, dev, u0, v0, precision, engine=None):
     """Relative L2 error against the exact solution after the workload's 200
     full steps, by Gauss quadrature (2m+2 points per axis, exact for the
     squared interpolant) over ACC_CELLS seeded random cells; the exact
@@ -331,6 +338,8 @@ def accuracy(hb, torch, dev, u0, v0, precision):
 
     h = 1.0 / N
     g = hb.Hermite(D, M, N, 1.0, h, LAM * h, hb.DISSIPATIVE, hb.PERIODIC, precision=precision)
+    if engine is not None:
+        g.set_split_engine(engine)
     du = torch.from_numpy(u0).to(dev)
     dv = torch.from_numpy(v0).to(dev)
     g.set_state_device(du, dv)
@@ -369,8 +378,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     fp64 = measure(hb, torch, dev, u0, v0, hb.FP64, args, ws, False)
-    split = measure(hb, torch, dev, u0, v0, hb.SPLIT32, args, ws, True)
+    split = measure(hb, torch, dev, u0, v0, hb.SPLIT32, args, ws, True, engine=0)
     fp64["g"].close()
+    tcm = measure(hb, torch, dev, u0, v0, hb.SPLIT32, args, ws, False, engine=1)
+    tcm["g"].close()
     # same start, same number of steps: difference of the two arithmetic paths
     a = np.concatenate([fp64["state"][0], fp64["state"][1]], 1)
     b = np.concatenate([split["state"][0], split["state"][1]], 1)
@@ -408,7 +419,33 @@ def run_ours(args):
     # matched L2 error: both arithmetics against the exact solution after the
     # workload's 200 steps (untimed)
     err64, T = accuracy(hb, torch, dev, u0, v0, hb.FP64)
-    errsp, _ = accuracy(hb, torch, dev, u0, v0, hb.SPLIT32)
+    errsp, _ = accuracy(hb, torch, dev, u0, v0, hb.SPLIT32, engine=0)
+    errtc, _ = accuracy(hb, torch, dev, u0, v0, hb.SPLIT32, engine=1)
+
+    # the other two spec workloads, compact (single GPU; untimed for the headline)
+    extra = {}
+    if ws == 1 and not args.no_extra:
+        by = batch_results(3, 2, variants=(hb.DISSIPATIVE,))
+        extra["batch2d"] = {
+            "workload": "ragged batch of 512 2-D dissipative problems (N in {32,64,128,256}^2, m in 2..6, "
+                        "periodic/Dirichlet/Neumann, 1-4 Gaussian pulses, c*dt/h=0.9), autotuned, graph-captured",
+            "unit": UNIT, "fp64": by["dissipative_fp64"], "split": by["dissipative_split"]}
+        from paper_1802_05246_b300.learned import SuperStepper
+
+        st = SuperStepper.load(LEARNED_WEIGHTS)
+        lr = learned_results(st, [1e-3, 1e-2], 3, 1, ((hb.FP64, "fp64"),))
+        extra["learned2d"] = {
+            "workload": "256 2-D periodic problems, m=3, N=128^2, c*dt/h=0.9, 1-6 Gaussian pulses, K=16 full "
+                        "steps per checked network advance, FP64 check and fallback",
+            "kappa": st.kappa, "plain_hermite_fp64_ms": lr["hermite_fp64_ms"],
+            "network_only_ms": lr["network_only_ms"],
+            "true_error_quantiles": {q: float(np.quantile(lr["e_true"], v))
+                                     for q, v in (("10%", 0.1), ("50%", 0.5), ("90%", 0.9))},
+            "bars": {f"{bar:.0e}": {"accepted": lr[(bar, "accepted_fp64")],
+                                    "false_accepts": lr[(bar, "false_accepts_fp64")],
+                                    "checked_advance_ms": lr[(bar, "learned_fp64_ms")],
+                                    "gain_vs_plain_fp64": lr["hermite_fp64_ms"] / lr[(bar, "learned_fp64_ms")]}
+                     for bar in (1e-3, 1e-2)}}
 
     if rank != 0:
         return 0
@@ -438,7 +475,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
         "config": {"workload": WORKLOAD, "d": D, "m": M, "N": N, "cfl": LAM, "variant": "dissipative",
                    "bc": "periodic", "precision": "split: FP32 hi+lo state and operator, three split products, "
-                                                  "compensated sums (HERMITE_SPLIT32)",
+                                                  "compensated sums (HERMITE_SPLIT32, CUDA-core engine)",
                    "step": "8 full time steps (16 half-steps) + 1 energy reduction",
                    "l2": "inputs larger than L2 (3.05 GB read+written per half-step vs 126 MB)",
                    "parallelism": f"replicas x{ws}"},
@@ -449,6 +486,13 @@ def run_ours(args):
                      "t": T, "full_steps": ACC_STEPS,
                      "measure": f"relative L2 of the I_m interpolant vs the exact solution, {ACC_CELLS} sampled "
                                 f"cells, {2 * M + 2}^3 Gauss points each"},
+        "split_tc": {"value": job_throughput(dof_per_step * args.steps, ws, tcm["ms"]),
+                     "ms_per_step": tcm["ms"] / args.steps, "dtype": "f32x2",
+                     "engine": "tensor cores (tcgen05): six BF16 data digits x seven operator digits, exact FP32 "
+                               "accumulation (hermite_set_split_engine 1)",
+                     "l2_err": errtc, "ratio_over_fp64": errtc / err64,
+                     "roofline": roofline("half_step_tc_kernel<3>", tcm["half_ms"], None, "tensor (BF16 digits)",
+                                          pk.get("bf16_tflops"), NODES * TC_FLOP_PER_NODE)},
         "fp64": {"value": value64, "ms_per_step": fp64["ms"] / args.steps, "dtype": "f64",
                  "roofline": roofline("half_step_f64_kernel<3,92>", fp64["half_ms"], TRAFFIC_PER_LAUNCH, "FP64",
                                       probe64),
@@ -464,6 +508,7 @@ def run_ours(args):
         # the plain energy int v^2 + c^2 |grad u|^2; the invariant (seminorm)
         # energy of smooth fine-grid data is rounding-level and not reported here
         "energy_plain_last": float(split["energy"][0]),
+        **extra,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -487,18 +532,18 @@ def batch_problems(seed=0, n=512, lam=0.9):
     return out
 
 
-def run_batch(args):
-    """Ragged batch of 512 2-D problems, both variants, FP64 and split."""
+def batch_results(steps, warmup, variants=(0, 1)):
+    """Ragged batch of 512 2-D problems: throughput of each variant in FP64 and
+    split precision at the autotuned item size and blocks per SM."""
     import torch
 
     import paper_1802_05246_b300 as hb
     from paper_1802_05246_b300 import inputs as I
 
-    torch.cuda.set_device(0)
     specs = batch_problems()
     lam = 0.9
     results = {}
-    for variant in (hb.DISSIPATIVE, hb.CONSERVATIVE):
+    for variant in variants:
         probs = [(2, m, Np, 1.0, 1.0 / Np, lam / Np, variant, bc) for (Np, m, bc, _, _, _) in specs]
         for prec in (hb.FP64, hb.SPLIT32):
             b = hb.HermiteBatch(probs, precision=prec)
@@ -508,17 +553,28 @@ def run_batch(args):
             for (Np, m, bc, cen, wid, amp), g in zip(specs, b.problems):
                 u0 = I.gaussian_data(2, m, Np, 1.0 / Np, bc, 0, cen, wid, amp)
                 g.set_state(u0, np.zeros((g.nodes(0), m * m)))
-            b.step(args.warmup)
+            b.step(warmup)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(s)
-            b.step(args.steps)
+            b.step(steps)
             e1.record(s)
             e1.synchronize()
             ms = e0.elapsed_time(e1)
-            results[(variant, prec)] = {"value": b.dof_per_step * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+            results[(variant, prec)] = {"value": b.dof_per_step * steps / (ms / 1e3), "ms_per_step": ms / steps,
                                         "autotune": {"item_nodes": items, "blocks_per_sm": blocks, "ms": tune_ms}}
             b.close()
+    return {f"{'dissipative' if v == 0 else 'conservative'}_{'fp64' if p == 0 else 'split'}": r
+            for (v, p), r in results.items()}
+
+
+def run_batch(args):
+    """Ragged batch of 512 2-D problems, both variants, FP64 and split."""
+    import torch
+
+    torch.cuda.set_device(0)
+    by = batch_results(args.steps, args.warmup)
+    results = {(0, 1): by["dissipative_split"]}
     line = {
         "metric": METRIC, "value": results[(0, 1)]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": results[(0, 1)]["ms_per_step"], "higher_is_better": True,
@@ -527,8 +583,7 @@ def run_batch(args):
                                "periodic/Dirichlet/Neumann, 1-4 Gaussian pulses, c*dt/h=0.9), one persistent "
                                "launch per size group per half-step, graph-captured full steps",
                    "step": "one full time step of all 512 problems"},
-        "by_variant_precision": {f"{'dissipative' if v == 0 else 'conservative'}_{'fp64' if p == 0 else 'split'}": r
-                                 for (v, p), r in results.items()},
+        "by_variant_precision": by,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -609,22 +664,21 @@ def run_paper3d(args):
 LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1802_05246_b300", "weights", "superstepper_k16.npz")
 
 
-def run_learned(args):
-    """Learned super-stepper against plain Hermite steps on 256 fresh 2-D
+def learned_results(st, bars, steps, warmup, precisions):
+    """The learned super-stepper against plain Hermite steps on 256 fresh 2-D
     problems (m = 3, 128^2 periodic, 1-6 Gaussian pulses, widths U[0.05,0.15]):
-    one benchmark step advances every problem by K = 16 full steps."""
+    one step advances every problem by K = 16 full steps, checked (one true
+    full step, residual estimate) and falling back to plain steps above the
+    bar.  Returns the timings, acceptance and false accepts per bar and check
+    precision, and the true K-step errors (evaluated untimed)."""
     import torch
 
     import paper_1802_05246_b300 as hb
-    from paper_1802_05246_b300.learned import SuperStepper
 
-    torch.cuda.set_device(0)
-    st = SuperStepper.load(args.weights)
-    B, bar = 256, args.bar
+    B = 256
     trajs = list(range(3_000_000, 3_000_000 + B))
     stream = torch.cuda.current_stream()
     zero_v = np.zeros((st.n, st.Nv))
-    work = B * st.K * 2 * st.n * st.C0  # DOF-updates of K full steps of all problems
 
     def fresh(prec):
         b = hb.HermiteBatch([st.problem] * B, precision=prec)
@@ -634,12 +688,12 @@ def run_learned(args):
         return b
 
     def timed(fn, before=None):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             if before:
                 before()
             fn()
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             if before:
                 before()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -652,25 +706,61 @@ def run_learned(args):
         return statistics.median(ms)
 
     e_true, resid = st.evaluate(trajs)  # untimed: the true K-step error of every prediction
-    res = {}
-    for prec, name in ((hb.FP64, "fp64"), (hb.SPLIT32, "split")):
+    res = {"work": B * st.K * 2 * st.n * st.C0, "e_true": e_true, "resid": resid}
+    for prec, name in precisions:
         b = fresh(prec)
         res[f"hermite_{name}_ms"] = timed(lambda: b.step(st.K))
         b.close()
         b = fresh(prec)
         X = st._alloc_states(B)
         st.gather(b, *X)
-        out = {}
+        for bar in bars:
+            out = {}
 
-        def run():
-            out["acc"], out["est"] = st.advance(b, bar=bar)
+            def run():
+                out["acc"], out["est"] = st.advance(b, bar=bar)
 
-        res[f"learned_{name}_ms"] = timed(run, before=lambda: st.scatter(b, *X))
-        res[f"accepted_{name}"] = float(np.mean(out["acc"]))
-        res[f"false_accepts_{name}"] = int(np.sum(out["acc"] & (e_true > bar)))
+            res[(bar, f"learned_{name}_ms")] = timed(run, before=lambda: st.scatter(b, *X))
+            res[(bar, f"accepted_{name}")] = float(np.mean(out["acc"]))
+            res[(bar, f"false_accepts_{name}")] = int(np.sum(out["acc"] & (e_true > bar)))
         A = st._alloc_states(B)
-        res[f"network_only_ms"] = timed(lambda: st.predict(X[0], X[1], A[0], A[1]))
+        res["network_only_ms"] = timed(lambda: st.predict(X[0], X[1], A[0], A[1]))
         b.close()
+    return res
+
+
+def run_learned(args):
+    """Learned super-stepper against plain Hermite steps on 256 fresh 2-D
+    problems (m = 3, 128^2 periodic, 1-6 Gaussian pulses, widths U[0.05,0.15]):
+    one benchmark step advances every problem by K = 16 full steps."""
+    import torch
+
+    import paper_1802_05246_b300 as hb
+    from paper_1802_05246_b300.learned import SuperStepper
+
+    torch.cuda.set_device(0)
+    st = SuperStepper.load(args.weights)
+    B, bar = 256, args.bar
+    stream = torch.cuda.current_stream()
+    r = learned_results(st, [bar], args.steps, args.warmup, ((hb.FP64, "fp64"), (hb.SPLIT32, "split")))
+    e_true, resid, work = r["e_true"], r["resid"], r["work"]
+    res = {k: v for k, v in r.items() if isinstance(k, str)}
+    res.update({k[1]: v for k, v in r.items() if isinstance(k, tuple)})
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
     # the dominant kernel: the 64 -> 64 forward convolution at the inference batch
     x = torch.zeros((B, 128, 128, 64), dtype=torch.bfloat16, device="cuda")
     y = torch.empty_like(x)
@@ -795,6 +885,7 @@ def main():
                     help="run one small case for an Nsight Compute capture instead of a benchmark")
     ap.add_argument("--variant", type=int, default=0, help="--ncu-case half_step_*: method variant")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing on the host cores")
+    ap.add_argument("--no-extra", action="store_true", help="skip the compact batch2d / learned2d sub-objects")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)

@@ -520,8 +520,32 @@ class SuperStepper:
         return st
 
 
+def recalibrate(path, quantile, ncal, log=print):
+    """Re-calibrate a trained super-stepper: kappa = the given quantile of
+    true error / residual over ncal held-out trajectories (seeds 10^6 ..),
+    checked on ncal further held-out trajectories (seeds 2 * 10^6 ..) at the
+    bars 1e-3 .. 1e-1; the new kappa is written back to `path`.  Returns the
+    verification table."""
+    st = SuperStepper.load(path)
+    e, r = st.calibrate(range(10 ** 6, 10 ** 6 + ncal), quantile=quantile)
+    log(f"calibration set ({ncal}): error/residual median {np.median(e / r):.3f}, "
+        f"{quantile:.3f} quantile {st.kappa:.3f}, max {np.max(e / r):.3f}")
+    e2, r2 = st.evaluate(range(2 * 10 ** 6, 2 * 10 ** 6 + ncal))
+    est = st.kappa * r2
+    table = {}
+    for bar in (1e-3, 3e-3, 1e-2, 3e-2, 1e-1):
+        acc = est <= bar
+        table[bar] = {"accepted": float(acc.mean()), "true_error_within": float(np.mean(e2 <= bar)),
+                      "false_accepts": int(np.sum(acc & (e2 > bar)))}
+        log(f"  verification bar {bar:.0e}: {table[bar]}")
+    st.save(path)
+    return table
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="Train the learned super-stepper on solver trajectories")
+    ap.add_argument("--recalibrate", default=None, help="only re-calibrate kappa of these trained weights")
+    ap.add_argument("--quantile", type=float, default=0.99, help="kappa quantile of true error / residual")
     ap.add_argument("--ntraj", type=int, default=10000)
     ap.add_argument("--nlev", type=int, default=5)
     ap.add_argument("--iters", type=int, default=20000)
@@ -529,9 +553,15 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--act", default="relu", help="comma-separated activations to train, each on the same data")
     ap.add_argument("--calib", type=int, default=256, help="held-out trajectories for the residual calibration")
-    ap.add_argument("--out", required=True, help="output path; with several activations, {act} is replaced")
+    ap.add_argument("--out", default=None, help="output path; with several activations, {act} is replaced")
     a = ap.parse_args(argv)
     import torch
+
+    if a.recalibrate:
+        recalibrate(a.recalibrate, a.quantile, a.calib)
+        return
+    if not a.out:
+        ap.error("--out is required for training")
 
     log = lambda s: print(s, flush=True)
     gen = SuperStepper()
@@ -547,9 +577,9 @@ def main(argv=None):
         st.train(levels, a.iters, batch=a.batch, lr=a.lr, log_every=max(1, a.iters // 40), log=log)
         torch.cuda.synchronize()
         log(f"[{act}] training: {a.iters} iterations in {time.time() - t0:.1f} s")
-        e, r = st.calibrate(range(10 ** 6, 10 ** 6 + a.calib))
+        e, r = st.calibrate(range(10 ** 6, 10 ** 6 + a.calib), quantile=a.quantile)
         log(f"[{act}] calibration set: true error median {np.median(e):.3e}, max {e.max():.3e}; "
-            f"error/residual median {np.median(e / r):.3f}, kappa (max) {st.kappa:.3f}")
+            f"error/residual median {np.median(e / r):.3f}, kappa ({a.quantile} quantile) {st.kappa:.3f}")
         out = a.out.replace("{act}", act)
         st.save(out)
         log(f"[{act}] saved {out}")
