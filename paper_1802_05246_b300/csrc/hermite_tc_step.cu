@@ -197,7 +197,7 @@ constexpr int kTcTileB = kTcCols * 32;               // 112 rows x 16 K, BF16
 constexpr int kTcBufA = kTcClasses * kTcDigits * kTcTileA;
 constexpr int kTcBufB = kTcClasses * kTcTileB;
 constexpr int kTcMaxNC = 8;
-constexpr size_t kTcSmem = 2 * (size_t)kTcBufA + 2 * (size_t)kTcBufB + kTcMaxNC * 128 * 4 + 4 * kTcMaxNC * 16 + 64;
+constexpr size_t kTcSmem = 2 * (size_t)kTcBufA + 2 * (size_t)kTcBufB + kTcMaxNC * 128 * 4 + 6 * kTcMaxNC * 16 + 64;
 
 struct TcArgs {
   Geometry g;
@@ -252,8 +252,9 @@ __device__ __forceinline__ void df_add_x2(float2 &ah, float2 &al, const float2 b
 }
 
 // Corner transform restricted to one group of four output classes, in
-// FP32 hi + lo on packed pairs: the values z_q for q = (4 g + cc) ^ p,
-// cc = 0..3, of corner data (xh, xl) with ghost signs applied.  3-D: the top
+// FP32 hi + lo on packed pairs: the values z_q of corner data (xh, xl) with
+// ghost signs applied, for the four q whose top bit (3-D) belongs to group g
+// and input class p, out[j] = z_q with q & 3 = j.  3-D: the top
 // corner bit of q is fixed by the group; 2-D: the full 4-point transform.
 template <int D>
 __device__ __forceinline__ void group_transform_x2(const float *xh, const float *xl, int gi, int p, float2 *out) {
@@ -283,9 +284,11 @@ __device__ __forceinline__ void group_transform_x2(const float *xh, const float 
   float2 mh = ph, ml = pl;
   df_add_x2(ph, pl, make_float2(sh.y, dh.y), make_float2(sl.y, dl.y));    // (z0, z1)
   df_add_x2(mh, ml, make_float2(-sh.y, -dh.y), make_float2(-sl.y, -dl.y));  // (z2, z3)
-  float2 zq[4] = {make_float2(ph.x, pl.x), make_float2(ph.y, pl.y), make_float2(mh.x, ml.x), make_float2(mh.y, ml.y)};
-#pragma unroll
-  for (int cc = 0; cc < 4; ++cc) out[cc] = zq[(cc ^ p) & 3];
+  // in the order of the low two bits of q; class 4 g + cc takes q = cc ^ (p & 3)
+  out[0] = make_float2(ph.x, pl.x);
+  out[1] = make_float2(ph.y, pl.y);
+  out[2] = make_float2(mh.x, ml.x);
+  out[3] = make_float2(mh.y, ml.y);
 }
 
 // Six signed 8-bit digits of two values at once (a packed pair: u = value of
@@ -341,8 +344,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
   unsigned char *Bbuf = Abuf + 2 * kTcBufA;                            // [2][class][112 x 16]
   float *mxs = reinterpret_cast<float *>(Bbuf + 2 * kTcBufB);          // [class][128]
   int16_t *s_inb = reinterpret_cast<int16_t *>(mxs + kTcMaxNC * 128);  // [NC][16]
-  int8_t *s_sh = reinterpret_cast<int8_t *>(s_inb + kTcMaxNC * 16);    // [NC][16]
-  uint64_t *bar = reinterpret_cast<uint64_t *>(s_sh + 2 * kTcMaxNC * 16);
+  int16_t *s_orow = s_inb + kTcMaxNC * 16;                             // [NC][16]
+  int8_t *s_er = reinterpret_cast<int8_t *>(s_orow + kTcMaxNC * 16);    // [NC][16] row exponent by (class, position)
+  int8_t *s_sh = s_er + kTcMaxNC * 16;                                 // [NC][16]
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s_sh + kTcMaxNC * 16);
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int node = tid & 127, half = tid >> 7;
@@ -351,6 +356,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
     const int b = a.inb[i];
     s_inb[i] = (int16_t)b;
     s_sh[i] = (int8_t)(b >= a.nu ? a.vexp : 0);
+    const int row = a.orow[i];
+    s_orow[i] = (int16_t)row;
+    s_er[i] = row >= 0 ? a.er[row] : (int8_t)0;
   }
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
@@ -410,10 +418,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         float x[NC], S = 0.f;
 #pragma unroll
         for (int s = 0; s < NC; ++s) {
-          float v = valid ? plane[idx[s]].x : 0.f;
-          if ((neg >> s) & 1) v = -v;
-          x[s] = v;
-          S += fabsf(v);
+          x[s] = valid ? plane[idx[s]].x : 0.f;
+          S += fabsf(x[s]);
+        }
+        if (neg) {
+#pragma unroll
+          for (int s = 0; s < NC; ++s)
+            if ((neg >> s) & 1) x[s] = -x[s];
         }
         transform_f32<D>(x);
         const float sc = pow2f(s_sh[p * 16 + half * 8 + kk]), slack = S * 9.5367431640625e-07f;
@@ -462,26 +473,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         uint4 *bdst = reinterpret_cast<uint4 *>(Bbuf + buf * kTcBufB);
         for (int i = tid; i < kTcBufB / 16; i += kTcThreads) bdst[i] = bsrc[i];
         const uint32_t neg = (uint32_t)(negm >> (8 * p)) & 0xFF;
+        // digit scales in the order of q: z_q goes to class cc = q ^ (p & 3)
+        float squ[kTcClasses], sqv[kTcClasses];
+#pragma unroll
+        for (int q = 0; q < kTcClasses; ++q) {
+          const int cc = q ^ (p & 3);
+          squ[q] = cc == 0 ? scu[0] : cc == 1 ? scu[1] : cc == 2 ? scu[2] : scu[3];
+          sqv[q] = cc == 0 ? scv[0] : cc == 1 ? scv[1] : cc == 2 ? scv[2] : scv[3];
+        }
         uint32_t pk[kTcClasses][kTcDigits][4];
         float dprev[kTcClasses][kTcDigits];
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+        // corner data of input kk + 1 are loaded while input kk is transformed
+        float2 xn[NC];
+        auto load_corners = [&](int kk) {
           const int b = s_inb[p * 16 + half * 8 + kk];
-          float xh[NC], xl[NC];
           const float2 *plane = a.src + (size_t)max(b, 0) * g.ld_src;
 #pragma unroll
+          for (int s = 0; s < NC; ++s) xn[s] = (valid && b >= 0) ? plane[idx[s]] : make_float2(0.f, 0.f);
+        };
+        load_corners(0);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          float xh[NC], xl[NC];
+#pragma unroll
           for (int s = 0; s < NC; ++s) {
-            float2 v = (valid && b >= 0) ? plane[idx[s]] : make_float2(0.f, 0.f);
-            if ((neg >> s) & 1) v = make_float2(-v.x, -v.y);
-            xh[s] = v.x;
-            xl[s] = v.y;
+            xh[s] = xn[s].x;
+            xl[s] = xn[s].y;
           }
+          if (neg) {  // ghost images (non-periodic boundaries only)
+#pragma unroll
+            for (int s = 0; s < NC; ++s)
+              if ((neg >> s) & 1) {
+                xh[s] = -xh[s];
+                xl[s] = -xl[s];
+              }
+          }
+          if (kk < 7) load_corners(kk + 1);
           float2 z[4];
           group_transform_x2<D>(xh, xl, gi, p, z);
           const bool isv = s_sh[p * 16 + half * 8 + kk] != 0;
           float d[kTcClasses][kTcDigits];
-          six_digits2(z[0], z[1], isv ? scv[0] : scu[0], isv ? scv[1] : scu[1], d[0], d[1]);
-          six_digits2(z[2], z[3], isv ? scv[2] : scu[2], isv ? scv[3] : scu[3], d[2], d[3]);
+          six_digits2(z[0], z[1], isv ? sqv[0] : squ[0], isv ? sqv[1] : squ[1], d[0], d[1]);
+          six_digits2(z[2], z[3], isv ? sqv[2] : squ[2], isv ? sqv[3] : squ[3], d[2], d[3]);
 #pragma unroll
           for (int cc = 0; cc < kTcClasses; ++cc)
 #pragma unroll
@@ -494,11 +527,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         }
         unsigned char *Ab = Abuf + buf * kTcBufA + tc::kmajor16_offset(node, half * 8);
 #pragma unroll
-        for (int cc = 0; cc < kTcClasses; ++cc)
+        for (int q = 0; q < kTcClasses; ++q) {
+          unsigned char *Aq = Ab + (q ^ (p & 3)) * kTcDigits * kTcTileA;
 #pragma unroll
           for (int i = 0; i < kTcDigits; ++i)
-            *reinterpret_cast<uint4 *>(Ab + (cc * kTcDigits + i) * kTcTileA) =
-                make_uint4(pk[cc][i][0], pk[cc][i][1], pk[cc][i][2], pk[cc][i][3]);
+            *reinterpret_cast<uint4 *>(Aq + i * kTcTileA) = make_uint4(pk[q][i][0], pk[q][i][1], pk[q][i][2], pk[q][i][3]);
+        }
         tc::fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -536,12 +570,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         for (int k = 0; k < kTcMDigits; ++k) tc::ld16(tmem + lane_base + cc * kTcCols + 16 * k, acc[k]);
 #pragma unroll
         for (int n = 0; n < 16; ++n) {
-          const int row = a.orow[c * 16 + n];
+          const int row = s_orow[c * 16 + n];
           if (row < 0) continue;
           float2 r = make_float2(acc[kTcMDigits - 1][n] * pow2f(-8 * (kTcMDigits - 1)), 0.f);
 #pragma unroll
           for (int k = kTcMDigits - 2; k >= 0; --k) r = dev::df_add(r, make_float2(acc[k][n] * pow2f(-8 * k), 0.f));
-          const float2 sc = pow2_split(Ec + a.er[row] - 16);
+          const float2 sc = pow2_split(Ec + s_er[c * 16 + n] - 16);
           r = make_float2(__fmul_rn(__fmul_rn(r.x, sc.x), sc.y), __fmul_rn(__fmul_rn(r.y, sc.x), sc.y));
           if (valid) {
             float2 *o = a.dst + (size_t)row * g.ld_dst + t;
