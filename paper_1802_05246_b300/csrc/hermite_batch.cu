@@ -49,6 +49,9 @@ __global__ void __launch_bounds__(kBT) batch_f64_kernel(const BatchDesc *__restr
   extern __shared__ __align__(16) double fsm[];
   double *Ms = fsm;              // [nci][CH]
   double *zb = Ms + CH * CH;     // [NC][kBT]  (nci <= nco <= CH)
+  // parity class of each output, beside the staged rows (in registers, CH of
+  // them pushed the 96-output instantiation past the register file)
+  int8_t *po = reinterpret_cast<int8_t *>(zb + NC * kBT);  // [CH]
   __shared__ int item_s;
   __shared__ int staged;         // problem whose operator Ms holds (-1: none)
   double *myz = zb + threadIdx.x;
@@ -65,14 +68,12 @@ __global__ void __launch_bounds__(kBT) batch_f64_kernel(const BatchDesc *__restr
         const int bb = e / CH, j = e % CH;
         Ms[e] = j < P.nco ? P.M[(size_t)j * P.nci + bb] : 0.0;
       }
+      for (int j = threadIdx.x; j < CH; j += kBT) po[j] = j < P.nco ? P.par[j] : 0;
       __syncthreads();
       if (threadIdx.x == 0) staged = I.prob;
     }
     const double *src = static_cast<const double *>(P.src);
     double *dst = static_cast<double *>(P.dst);
-    int po[CH];
-#pragma unroll
-    for (int j = 0; j < CH; ++j) po[j] = j < P.nco ? P.par[j] : 0;
     for (int64_t t = I.n0 + threadIdx.x; t < I.n1; t += kBT) {
       int64_t idx[NC];
       int gm[NC];
@@ -447,7 +448,7 @@ int launch_group(hermite_batch *b, int k, const hermite_batch::Group &gr, unsign
   } else {
 #define HERMITE_BATCH_F64(CH_)                                                                              \
   if (gr.tmpl == CH_) {                                                                                     \
-    const size_t smem = sizeof(double) * ((size_t)CH_ * CH_ + (1 << D) * kBT);                              \
+    const size_t smem = sizeof(double) * ((size_t)CH_ * CH_ + (1 << D) * kBT) + CH_;                        \
     if (smem > 40 * 1024 &&                                                                                 \
         !bok(b, cudaFuncSetAttribute(batch_f64_kernel<D, CH_>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                      (int)smem),                                                            \

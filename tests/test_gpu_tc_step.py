@@ -100,3 +100,42 @@ def test_tc_engine_accuracy_bar_3d_pulses(hb):
     etc = pulse_errors(hb, 32, hb.SPLIT32, engine=1)
     assert e64 >= 1e-9 and etc <= 1.2 * e64
     assert abs(etc - e64) <= 1e-3 * e64
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_tc_engine_full_size_3d_sampled(hb, orc, variant):
+    """The 3-D workload at its full size (m = 3, 128^3, c dt/h = 0.9, eight
+    seeded pulses) on the tensor-core engine, launched as the benchmark's
+    split_tc arm launches it: two half-steps, 600 sampled targets of each
+    recomputed by the oracle from the GPU's input level."""
+    d, m, N = 3, 3, 128
+    h = 1.0 / N
+    g = hb.Hermite(d, m, N, 1.0, h, 0.9 * h, variant, 0, precision=hb.SPLIT32)
+    g.set_split_engine(1)
+    P = orc.Problem(d, m, N, 1.0, h, 0.9 * h, variant, 0)
+    from paper_1802_05246_b300 import inputs as I
+
+    cen, wid, amp = I.pulses_3d_config(0)
+    u0 = I.gaussian_data(d, m, N, h, 0, 0, cen, wid, amp)
+    v0 = np.zeros((N ** 3, m ** 3))
+    g.set_state(u0, v0)
+    rng = np.random.default_rng(12)
+    t = np.concatenate([rng.integers(0, N ** 3, 600), [0, N ** 3 - 1, N - 1, N * N - 1]])
+    if variant == orc.CONSERVATIVE:
+        q0, _ = g.get_grid(1)
+        g.advance_half(1)
+        p1, _ = g.get_grid(0)
+        assert rel_l2(p1[t], P.half_step_sample(0, q0, None, t, old_u=u0[t])) <= TOL_SPLIT
+        g.advance_half(1)
+        q1, _ = g.get_grid(1)
+        assert rel_l2(q1[t], P.half_step_sample(1, p1, None, t, old_u=q0[t])) <= TOL_SPLIT
+    else:
+        g.advance_half(1)
+        du, dv = g.get_grid(1)
+        wu, wv = P.half_step_sample(1, u0, v0, t)
+        assert rel_l2(np.concatenate([du[t], dv[t]], 1), np.concatenate([wu, wv], 1)) <= TOL_SPLIT
+        g.advance_half(1)
+        pu, pv = g.get_grid(0)
+        wu, wv = P.half_step_sample(0, du, dv, t)
+        assert rel_l2(np.concatenate([pu[t], pv[t]], 1), np.concatenate([wu, wv], 1)) <= TOL_SPLIT
+    g.close()
