@@ -418,9 +418,12 @@ def run_ours(args):
 
     # matched L2 error: both arithmetics against the exact solution after the
     # workload's 200 steps (untimed)
-    err64, T = accuracy(hb, torch, dev, u0, v0, hb.FP64)
-    errsp, _ = accuracy(hb, torch, dev, u0, v0, hb.SPLIT32, engine=0)
-    errtc, _ = accuracy(hb, torch, dev, u0, v0, hb.SPLIT32, engine=1)
+    if args.no_accuracy:
+        err64 = errsp = errtc = T = float("nan")
+    else:
+        err64, T = accuracy(hb, torch, dev, u0, v0, hb.FP64)
+        errsp, _ = accuracy(hb, torch, dev, u0, v0, hb.SPLIT32, engine=0)
+        errtc, _ = accuracy(hb, torch, dev, u0, v0, hb.SPLIT32, engine=1)
 
     # the other two spec workloads, compact (single GPU; untimed for the headline)
     extra = {}
@@ -886,6 +889,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="--ncu-case half_step_*: method variant")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing on the host cores")
     ap.add_argument("--no-extra", action="store_true", help="skip the compact batch2d / learned2d sub-objects")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the 200-step error measurements against the exact solution (profiling runs)")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)
