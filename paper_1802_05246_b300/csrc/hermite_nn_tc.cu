@@ -32,6 +32,7 @@
 #include "hermite.h"
 #include "hermite_nn.h"
 #include "hermite_nn_internal.h"
+#include "hermite_tc.cuh"
 
 namespace hermite_nn {
 namespace {
@@ -41,15 +42,9 @@ typedef __nv_bfloat16 bf16;
 constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait polls before a wait is declared failed
 constexpr int kMaxTcDil = 8;               // largest dilation of the tensor-core kernel (boundary rows)
 
-__device__ __forceinline__ uint32_t saddr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+using hermite::tc::saddr;
 
 // ---- mbarrier ----------------------------------------------------------------
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(b)), "r"(bytes) : "memory");
 }
@@ -57,18 +52,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(b)) : "memory");
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-  const uint32_t a = saddr(b);
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
+  return hermite::tc::mbar_wait(b, parity, kWaitLimit);
 }
+using hermite::tc::mbar_fence_init;
+using hermite::tc::mbar_init;
 
 // ---- TMA ------------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, uint64_t *bar) {
@@ -80,44 +67,7 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, in
 }
 
 // ---- tcgen05 ------------------------------------------------------------------------
-__device__ __forceinline__ void tc_alloc(uint32_t *slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(slot)), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tc_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-// D[tmem] (+)= A[smem] * B[smem]^T, both K-major
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// arrive on the mbarrier once every tcgen05 operation issued so far by this thread has completed
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(bar))
-               : "memory");
-}
-// 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes (one lane per thread); the
-// wait is in the same statement so no register is read before the load lands
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+namespace tc = hermite::tc;
 
 // three 32-column loads under one wait (the epilogue's D_0, D_2 and D_1)
 __device__ __forceinline__ void tc_ld32x3(uint32_t t0, uint32_t t1, uint32_t t2, float (&a)[32], float (&b)[32],
@@ -152,11 +102,7 @@ __device__ __forceinline__ uint64_t sw128_desc(const void *tile) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator [4,6) = 1, A and B BF16
-// [7,10) = [10,13) = 1, both K-major, N >> 3 at [17,23), M >> 4 at [24,29).
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
+using hermite::tc::idesc_bf16;
 
 // the 16-byte chunk c of row r of a 128-byte-swizzled tile
 __device__ __forceinline__ uint32_t sw128_offset(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
@@ -206,36 +152,36 @@ __global__ void __launch_bounds__(128) tc_gemm_selftest_kernel(const bf16 *__res
     mbar_fence_init();
   }
   if (warp == 0) {
-    tc_alloc(slot, 64);
-    tc_relinquish();
+    tc::alloc(slot, 64);
+    tc::relinquish();
   }
-  tc_fence_before();
+  tc::fence_before();
   __syncthreads();
-  tc_fence_after();
+  tc::fence_after();
   const uint32_t tmem = *slot;
   if (tid == 0) {
     const uint64_t da = sw128_desc(As), db = sw128_desc(Bs);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) tc_mma(tmem, da + 2 * k, db + 2 * k, idesc_bf16(128, N), k > 0 ? 1u : 0u);
-    tc_commit(bar);
+    for (int k = 0; k < 4; ++k) tc::mma(tmem, da + 2 * k, db + 2 * k, idesc_bf16(128, N), k > 0 ? 1u : 0u);
+    tc::commit(bar);
   }
   const bool ok = mbar_wait(bar, 0);
-  tc_fence_after();
+  tc::fence_after();
   if (ok) {
     const int row = warp * 32 + lane;
 #pragma unroll
     for (int c0 = 0; c0 < N; c0 += 16) {
       float v[16];
-      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
 #pragma unroll
       for (int j = 0; j < 16; ++j) D[row * N + c0 + j] = v[j];
     }
   } else if (lane == 0) {
     atomicExch(status, 1);
   }
-  tc_fence_before();
+  tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc_dealloc(tmem, 64);
+  if (warp == 0) tc::dealloc(tmem, 64);
 }
 
 // ---------------------------------------------------------------------------
@@ -304,12 +250,12 @@ __global__ void __launch_bounds__(320, 1)
     mbar_fence_init();
   }
   if (warp == 1) {
-    tc_alloc(slot, C::TMEM_COLS);
-    tc_relinquish();
+    tc::alloc(slot, C::TMEM_COLS);
+    tc::relinquish();
   }
-  tc_fence_before();
+  tc::fence_before();
   __syncthreads();
-  tc_fence_after();
+  tc::fence_after();
   const uint32_t tmem = *slot;
 
   if (warp == 0) {
@@ -346,7 +292,7 @@ __global__ void __launch_bounds__(320, 1)
           atomicExch(&s_err, 1);
           break;
         }
-        tc_fence_after();
+        tc::fence_after();
         const uint32_t dacc = tmem + (uint32_t)(a * C::ACC);
         bool ok = true;
         for (int ky = 0; ky < 3; ++ky, ++it) {
@@ -355,21 +301,21 @@ __global__ void __launch_bounds__(320, 1)
             ok = false;
             break;
           }
-          tc_fence_after();
+          tc::fence_after();
           const uint64_t da = sw128_desc(As + s * C::A_BYTES);
           const uint64_t dw = sw128_desc(Ws + 3 * ky * COUT * 128);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) tc_mma(dacc, da + 2 * kk, dw + 2 * kk, C::IDESC, (ky | kk) ? 1u : 0u);
-          tc_commit(empty + s);  // the stage is free once these MMAs have read it
+          for (int kk = 0; kk < 4; ++kk) tc::mma(dacc, da + 2 * kk, dw + 2 * kk, C::IDESC, (ky | kk) ? 1u : 0u);
+          tc::commit(empty + s);  // the stage is free once these MMAs have read it
         }
         if (!ok) {
           atomicExch(&s_err, 1);
           break;
         }
-        tc_commit(tfull + a);
+        tc::commit(tfull + a);
       }
       // every MMA this thread issued has completed before tensor memory is released
-      tc_commit(drain);
+      tc::commit(drain);
       if (!mbar_wait(drain, 0)) atomicExch(&s_err, 1);
     }
   } else {
@@ -390,17 +336,17 @@ __global__ void __launch_bounds__(320, 1)
       // all epilogue warps leave together; this barrier also orders the previous
       // row's exchange reads before this row's exchange writes
       if (named_sync_or(1, C::EPI, !ok || read_flag(&s_err))) break;
-      tc_fence_after();
+      tc::fence_after();
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * C::ACC + cb);
       float acc[C::CH], d0[C::CH], d2[C::CH];
       if constexpr (C::CH == 32) {
         tc_ld32x3(tbase, tbase + 2 * COUT, tbase + COUT, d0, d2, acc);
       } else {
-        tc_ld16(tbase, d0);
-        tc_ld16(tbase + 2 * COUT, d2);
-        tc_ld16(tbase + COUT, acc);
+        tc::ld16(tbase, d0);
+        tc::ld16(tbase + 2 * COUT, d2);
+        tc::ld16(tbase + COUT, acc);
       }
-      tc_fence_before();
+      tc::fence_before();
       mbar_arrive(tempty + a);
 #pragma unroll
       for (int j = 0; j < C::CH; j += 4) {
@@ -450,9 +396,9 @@ __global__ void __launch_bounds__(320, 1)
       }
     }
   }
-  tc_fence_before();
+  tc::fence_before();
   __syncthreads();
-  if (warp == 1) tc_dealloc(tmem, C::TMEM_COLS);
+  if (warp == 1) tc::dealloc(tmem, C::TMEM_COLS);
   if (tid == 0 && read_flag(&s_err)) atomicExch(&g_tc_status, 1);
 }
 

@@ -1,7 +1,7 @@
 // Thin inline-PTX wrappers for the fifth-generation tensor cores (tcgen05),
-// mbarriers and shared-memory matrix descriptors, as used by the
-// tensor-core half-step.  Every wait is bounded: it returns false after
-// kWaitLimit polls instead of spinning forever.
+// mbarriers and shared-memory matrix descriptors, shared by the tensor-core
+// half-step and the learned stepper's tensor-core convolution.  Every wait is
+// bounded: it returns false after `limit` polls instead of spinning forever.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,9 +20,9 @@ __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(b)), "r"(count) : "memory");
 }
 __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint32_t limit = kWaitLimit) {
   const uint32_t a = saddr(b);
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -320,17 +320,20 @@ def _boundary_targets(rng, n, count):
 _BC_DATA = {}
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 @pytest.mark.parametrize("bc", [1, 2])
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_full_size_3d_boundaries_sampled(hb, orc, variant, bc, precision):
     """3-D m=3, 96^3 cells (97^3 primal nodes) with Dirichlet or Neumann
-    boundaries, every variant, FP64 and split: two half-steps from seeded odd
-    or even Gaussian-pulse data, sampled targets (all corners, faces, edges)
+    boundaries, every variant, FP64 (0), split on the CUDA cores (1) and split
+    on the tensor cores (2): two half-steps from seeded odd or even
+    Gaussian-pulse data, sampled targets (all corners, faces, edges)
     recomputed by the oracle from the GPU's input level."""
     d, m, N = 3, 3, 96
     h = 1.0 / N
-    g = hb.Hermite(d, m, N, 1.0, h, 0.9 * h, variant, bc, precision=precision)
+    g = hb.Hermite(d, m, N, 1.0, h, 0.9 * h, variant, bc, precision=min(precision, 1))
+    if precision > 0:
+        g.set_split_engine(precision - 1)
     P = orc.Problem(d, m, N, 1.0, h, 0.9 * h, variant, bc)
     if (N, bc) not in _BC_DATA:
         cen, wid, amp = I.pulses_3d_config(1)
