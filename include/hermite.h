@@ -247,7 +247,8 @@ int hermite_peak_probe(int kind, double *flops_per_s);
  *   1  tensor cores (tcgen05): exact products of BF16 digits of both operands
  *      with FP32 accumulation, available where d >= 2 and every parity class
  *      of inputs and of outputs is at most 16 coefficients wide (3-D m <= 3,
- *      2-D m <= 4).
+ *      2-D m <= 4), for contexts of hermite_create / hermite_create_ex (not
+ *      for the problems of a batch, which run the batch kernels).
  * HERMITE_ERR_STATE for an FP64 context, HERMITE_ERR_UNSUPPORTED if engine 1
  * is asked for a shape it does not cover, HERMITE_ERR_ARG otherwise bad.
  * hermite_get_split_engine returns the engine in use (-1: not a split context). */

@@ -314,7 +314,8 @@ int create_context(int d, int m, int64_t N, double c, double h, double dt, int v
       if (!cuda_ok(ctx, cudaMemset(ctx->fgrid[g], 0, sizeof(float2) * ctx->ncoef * ctx->ld[g]), "memset"))
         rc = HERMITE_ERR_CUDA;
     if (rc == HERMITE_OK) rc = build_split_operator(ctx);
-    if (rc == HERMITE_OK) rc = build_tc_operator(ctx);
+    // batch problems (built without energy forms) run the batch kernels only
+    if (rc == HERMITE_OK && with_energy) rc = build_tc_operator(ctx);
     if (rc == HERMITE_OK) rc = build_split_forms(ctx);
     if (cons) alloc((void **)&ctx->fscratch, sizeof(float2) * ctx->Nu * maxld, "split scratch");
   }
