@@ -139,3 +139,26 @@ def test_tc_engine_full_size_3d_sampled(hb, orc, variant):
         wu, wv = P.half_step_sample(0, du, dv, t)
         assert rel_l2(np.concatenate([pu[t], pv[t]], 1), np.concatenate([wu, wv], 1)) <= TOL_SPLIT
     g.close()
+
+
+@pytest.mark.parametrize("d,m,N,c,variant,bc", [(3, 3, 5, 2.3, 0, 0), (2, 4, 7, 0.37, 0, 1), (3, 2, 5, 5.0, 1, 2)])
+def test_tc_engine_wave_speed(hb, orc, d, m, N, c, variant, bc):
+    """Wave speeds c != 1 change the velocity scaling h/c that balances the
+    u and v digits (2^vexp): parity with the oracle as for c = 1."""
+    h = 1.0 / N
+    dt = 0.9 * h / c
+    g = hb.Hermite(d, m, N, c, h, dt, variant, bc, precision=hb.SPLIT32)
+    g.set_split_engine(1)
+    P = orc.Problem(d, m, N, c, h, dt, variant, bc)
+    u0, v0 = _state(P, 99)
+    v0 = v0 * c / h  # velocity data of the size a wave of speed c carries
+    g.set_state(u0, v0)
+    g.step(2)
+    gu, gv = g.get_state()
+    if variant == orc.CONSERVATIVE:
+        ou, _ = P.run(u0, nsteps=2, dual_u=P.cons_start(u0, v0))
+        assert rel_l2(gu, ou) <= TOL_SPLIT
+    else:
+        ou, ov = P.run(u0, v0, nsteps=2)
+        assert rel_l2(np.concatenate([gu, gv * h / c], 1), np.concatenate([ou, ov * h / c], 1)) <= TOL_SPLIT
+    g.close()
