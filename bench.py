@@ -8,15 +8,21 @@ U[0.05,0.1], amplitudes N(0,1), numpy PCG64 seed 0), v0 = 0, dissipative
 
 One benchmark step = one pass of the whole hot path: 8 full time steps
 (16 fused half-step launches) followed by one energy reduction (the energy
-is a diagnostic taken every 8 steps).  Both arithmetic paths run the same
-steps from the same state: `value` is the split-precision path (FP32 hi+lo,
-within 1.2x of the FP64 error wherever that error is >= 1e-9, see the tests),
-and the FP64 path is reported beside it with the difference of the two
-states after the same steps.  One DOF-update = one stored scaled
+is a diagnostic taken every 8 steps).  The arithmetic paths run the same
+steps from the same state: `value` is the split-precision path on the CUDA
+cores (FP32 hi+lo); `split_tc` the same arithmetic with its products on the
+tensor cores; `fp64` the FP64 path.  `accuracy` gives each path's relative
+L2 error against the exact solution after the workload's 200 full steps
+(the "matched L2 error" of the metric).  One DOF-update = one stored scaled
 coefficient of one node written by one half-step.  The 3 GB state is far
-larger than the 126 MB L2, so no flush is needed between steps.
+larger than the 126 MB L2, so no flush is needed between steps.  The line
+also carries compact results of the two other workloads (`batch2d`: 512
+ragged 2-D problems; `learned2d`: the learned super-stepper at the bars 1e-3
+and 1e-2) and the oracle timed on the host cores (`cpu_baseline`).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--workload grid3d|batch2d|learned2d|paper3d] [--no-extra] [--no-accuracy]
+       [--no-cpu-baseline] [--ncu-case NAME [--variant V]]
 For N > 1 launch with torch.distributed.run; each rank runs an independent
 replica (the method needs no data-path collective here), the slowest rank's
 time counts and `value` aggregates all ranks.
