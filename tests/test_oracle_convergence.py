@@ -111,3 +111,33 @@ def test_2d_plane_wave_order(orc, variant, lam, m):
     else:
         p = 2 * m if lam == 1.0 else 2 * m - 1
     assert _slope(Ns, errs) >= p - 0.35, (errs, _slope(Ns, errs))
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("lam", [0.5, 0.7])
+def test_conservative_truncation_constant(orc, m, lam):
+    """Sec. 4.4 (Eq. Ctrunc): the one-step error of the conservative update
+    from exact data (primal level at 0, dual level at dt/2, target at dt) is
+    2^-(2m+1) h^(2m+2) (lam^2 - 1)^(m+1) u^(2m+2) / (2m+2)! to leading order:
+    the cosine propagator acts on a polynomial by d'Alembert's formula,
+    2 C f(0) = f(c dt/2) + f(-c dt/2), and the interpolation error is
+    -(x^2 - h^2/4)^(m+1) u^(2m+2) / (2m+2)! (Eq. Imtrunc).  This is Eq. Ctrunc
+    with (c dt)^2 in place of (c dt / 2)^2; the lam- and m-dependence are the
+    paper's.  u = sin x cos t, h = 2 pi / N: the ratio of the error to this
+    constant tends to 1 at the rate h^2."""
+    ratios = []
+    for N in (16, 32):
+        h = 2 * np.pi / N
+        dt = lam * h
+        P = orc.Problem(1, m, N, 1.0, h, dt, orc.CONSERVATIVE, orc.PERIODIC)
+        p0 = I.sine_data(1, m, N, h, 0, 0, [1.0])
+        q = math.cos(dt / 2) * I.sine_data(1, m, N, h, 0, 1, [1.0])
+        new = P.half_step(0, q, dst_u=p0)
+        ex = math.cos(dt) * I.sine_data(1, m, N, h, 0, 0, [1.0])
+        err = ex[:, 0] - new[:, 0]
+        lead = 2.0 ** (-(2 * m + 1)) * h ** (2 * m + 2) * (lam**2 - 1) ** (m + 1) / math.factorial(2 * m + 2)
+        pred = lead * (-1) ** (m + 1) * np.sin(np.arange(N) * h)  # u^(2m+2) of sin x
+        i = int(np.argmax(np.abs(pred)))
+        ratios.append(err[i] / pred[i])
+    assert abs(ratios[1] - 1) <= 0.02, ratios
+    assert abs(ratios[1] - 1) < abs(ratios[0] - 1), ratios
