@@ -141,3 +141,27 @@ def test_conservative_truncation_constant(orc, m, lam):
         ratios.append(err[i] / pred[i])
     assert abs(ratios[1] - 1) <= 0.02, ratios
     assert abs(ratios[1] - 1) < abs(ratios[0] - 1), ratios
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("lam", [0.5, 0.7, 0.9])
+def test_dissipative_truncation_constant_nu(orc, m, lam):
+    """Sec. 3.2 (Eq. vtrunc): with u = 0 and v = sin x at t = 0 only the
+    velocity term of the half-step's velocity error survives,
+    lam h/2 * nu h^(2m-1) v^(2m) with nu = 2^-(2m-1) / (2m)! (lam^2-1)^m / lam;
+    the ratio of the oracle's error at the dual nodes to it tends to 1."""
+    ratios = []
+    for N in (16, 32):
+        h = 2 * np.pi / N
+        dt = lam * h
+        P = orc.Problem(1, m, N, 1.0, h, dt, orc.DISSIPATIVE, orc.PERIODIC)
+        v0 = I.sine_data(1, m - 1, N, h, 0, 0, [1.0])
+        _, dv = P.half_step(1, np.zeros((N, m + 1)), v0)
+        xd = (np.arange(N) + 0.5) * h
+        err = math.cos(dt / 2) * np.sin(xd) - dv[:, 0]
+        nu = 2.0 ** (-(2 * m - 1)) / math.factorial(2 * m) * (lam**2 - 1) ** m / lam
+        pred = lam * h / 2 * nu * h ** (2 * m - 1) * (-1) ** m * np.sin(xd)
+        i = int(np.argmax(np.abs(pred)))
+        ratios.append(err[i] / pred[i])
+    assert abs(ratios[1] - 1) <= 0.005, ratios
+    assert abs(ratios[1] - 1) < abs(ratios[0] - 1), ratios
