@@ -629,8 +629,10 @@ def run_paper3d(args):
         # "points per direction": n nodes per axis on the primal grid
         N = n if bc == hb.PERIODIC else n - 1
         h = 1.0 / N
-        for prec in (hb.FP64, hb.SPLIT32):
+        for prec, engine in ((hb.FP64, None), (hb.SPLIT32, 0), (hb.SPLIT32, 1)):
             g = hb.Hermite(3, m, N, 1.0, h, 0.9 * h, vid[vname], bc, precision=prec)
+            if engine is not None:
+                g.set_split_engine(engine)
             n0 = g.nodes(0)
             u = torch.randn((n0, g.Nu), dtype=torch.float64, device="cuda", generator=gen)
             v = torch.randn((n0, g.Nv), dtype=torch.float64, device="cuda", generator=gen) if g.Nv else None
@@ -648,7 +650,8 @@ def run_paper3d(args):
             ms = e0.elapsed_time(e1) / args.steps
             dof = (g.nodes(0) + g.nodes(1)) * (g.Nu + g.Nv)  # DOF-updates of one full step
             out.append({"variant": vname, "m": m, "points": n, "bc": ["periodic", "dirichlet", "neumann"][bc],
-                        "precision": ["fp64", "split"][prec], "ms_per_full_step": ms,
+                        "precision": "fp64" if engine is None else ("split" if engine == 0 else "split_tc"),
+                        "ms_per_full_step": ms,
                         "dof_updates_per_s": dof / (ms / 1e3),
                         "p100_s_per_iteration": p100,
                         "speedup_vs_p100": (p100 * 1e3 / ms) if p100 else None})

@@ -347,8 +347,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
   int16_t *s_orow = s_inb + kTcMaxNC * 16;                             // [NC][16]
   int8_t *s_er = reinterpret_cast<int8_t *>(s_orow + kTcMaxNC * 16);    // [NC][16] row exponent by (class, position)
   int8_t *s_sh = s_er + kTcMaxNC * 16;                                 // [NC][16]
-  uint64_t *bar = reinterpret_cast<uint64_t *>(s_sh + kTcMaxNC * 16);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s_sh + kTcMaxNC * 16);   // [2] MMAs of a buffer done
+  uint64_t *bar_b = bar + 2;                                            // [2] operator chunk arrived
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 4);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int node = tid & 127, half = tid >> 7;
   const Geometry &g = a.g;
@@ -363,6 +364,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
     tc::mbar_init(&bar[1], 1);
+    tc::mbar_init(&bar_b[0], 1);
+    tc::mbar_init(&bar_b[1], 1);
     tc::mbar_fence_init();
   }
   if (warp == 0) {
@@ -376,6 +379,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   uint32_t it = 0;  // K chunks whose MMAs this CTA has issued
   bool failed = false;
+  bool tfail = false;  // thread 0: an operator-chunk wait ran out
   const int64_t ntiles = (g.nodes_dst + 127) / 128;
   for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int64_t t = tile * 128 + node;
@@ -464,14 +468,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         const int buf = it & 1;
         if (it >= 2) {
           const bool ok = tc::mbar_wait(&bar[buf], ((it >> 1) - 1) & 1);
-          if (__syncthreads_or(!ok)) {
+          if (__syncthreads_or(!ok || tfail)) {
             failed = true;
             break;
           }
         }
-        const uint4 *bsrc = a.Bimg + (size_t)(gi * NC + p) * (kTcBufB / 16);
-        uint4 *bdst = reinterpret_cast<uint4 *>(Bbuf + buf * kTcBufB);
-        for (int i = tid; i < kTcBufB / 16; i += kTcThreads) bdst[i] = bsrc[i];
+        // this chunk's operator digits arrive asynchronously while the
+        // threads produce the data digits; only the MMA issuer waits for them
+        if (tid == 0) {
+          tc::mbar_expect_tx(&bar_b[buf], kTcBufB);
+          tc::bulk_g2s(Bbuf + buf * kTcBufB, a.Bimg + (size_t)(gi * NC + p) * (kTcBufB / 16), kTcBufB, &bar_b[buf]);
+        }
         const uint32_t neg = (uint32_t)(negm >> (8 * p)) & 0xFF;
         // digit scales in the order of q: z_q goes to class cc = q ^ (p & 3)
         float squ[kTcClasses], sqv[kTcClasses];
@@ -509,12 +516,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
               }
           }
           if (kk < 7) load_corners(kk + 1);
-          float2 z[4];
-          group_transform_x2<D>(xh, xl, gi, p, z);
-          const bool isv = s_sh[p * 16 + half * 8 + kk] != 0;
           float d[kTcClasses][kTcDigits];
-          six_digits2(z[0], z[1], isv ? sqv[0] : squ[0], isv ? sqv[1] : squ[1], d[0], d[1]);
-          six_digits2(z[2], z[3], isv ? sqv[2] : squ[2], isv ? sqv[3] : squ[3], d[2], d[3]);
+          // positions past the class's inputs are zero padding (the same for
+          // the whole warp): their digits are zero without any arithmetic
+          if (s_inb[p * 16 + half * 8 + kk] >= 0) {
+            float2 z[4];
+            group_transform_x2<D>(xh, xl, gi, p, z);
+            const bool isv = s_sh[p * 16 + half * 8 + kk] != 0;
+            six_digits2(z[0], z[1], isv ? sqv[0] : squ[0], isv ? sqv[1] : squ[1], d[0], d[1]);
+            six_digits2(z[2], z[3], isv ? sqv[2] : squ[2], isv ? sqv[3] : squ[3], d[2], d[3]);
+          } else {
+#pragma unroll
+            for (int cc = 0; cc < kTcClasses; ++cc)
+#pragma unroll
+              for (int i = 0; i < kTcDigits; ++i) d[cc][i] = 0.f;
+          }
 #pragma unroll
           for (int cc = 0; cc < kTcClasses; ++cc)
 #pragma unroll
@@ -535,18 +551,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         }
         tc::fence_async_smem();
         __syncthreads();
-        if (tid == 0) {
+        // thread 0 waits for the operator chunk, then issues; a wait that runs
+        // out is reported at the next block barrier (the other threads go on)
+        if (tid == 0 && !tc::mbar_wait(&bar_b[buf], (it >> 1) & 1)) tfail = true;
+        if (tid == 0 && !tfail) {
           tc::fence_after();
+          // digit-major order: consecutive MMAs go to different classes'
+          // accumulators, which do not depend on one another
 #pragma unroll
-          for (int cc = 0; cc < kTcClasses; ++cc) {
-            const uint64_t db = tc::desc_kmajor(Bbuf + buf * kTcBufB + cc * kTcTileB, 128, 256);
+          for (int i = 0; i < kTcDigits; ++i)
 #pragma unroll
-            for (int i = 0; i < kTcDigits; ++i) {
+            for (int cc = 0; cc < kTcClasses; ++cc) {
+              const uint64_t db = tc::desc_kmajor(Bbuf + buf * kTcBufB + cc * kTcTileB, 128, 256);
               const uint64_t da = tc::desc_kmajor(Abuf + buf * kTcBufA + (cc * kTcDigits + i) * kTcTileA, 128, 256);
               tc::mma(tmem + cc * kTcCols + 16 * i, da, db, tc::idesc_bf16(128, 16 * (kTcMDigits - i)),
                       (p > 0 || i > 0) ? 1u : 0u);
             }
-          }
           tc::commit(&bar[buf]);
         }
       }
@@ -554,7 +574,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
       // ---- epilogue: the seven diagonals of each class -> FP32 hi + lo outputs
       {
         const uint32_t last = it - 1;
-        const bool ok = tc::mbar_wait(&bar[last & 1], (last >> 1) & 1);
+        const bool ok = !tfail && tc::mbar_wait(&bar[last & 1], (last >> 1) & 1);
         if (__syncthreads_or(!ok)) {
           failed = true;
           break;
