@@ -124,3 +124,19 @@ def test_split_accuracy_bar_3d_pulses(hb, N):
     assert esp <= 1.2 * e64, (N, e64, esp)
     # and the two arithmetics agree far below the discretisation error
     assert abs(esp - e64) <= 1e-3 * e64
+
+
+def test_3d_pulse_workload_converges_at_order_2m_minus_1(hb):
+    """The 3-D workload (m = 3, c dt/h = 0.9, the eight seeded pulses) run to
+    the same time T = 1.40625 on 32^3, 48^3 and 64^3 cells: the FP64 error
+    against the exact solution falls at the order 2m - 1 = 5 that Eq. vtrunc
+    predicts for lambda < 1 (its nu h^(2m-1) term dominates), within [4.5, 6]."""
+    import math
+
+    T, lam = 1.40625, 0.9
+    errs = []
+    for N in (32, 48, 64):
+        steps = int(round(T / (lam / N)))
+        errs.append(pulse_errors(hb, N, hb.FP64, nsteps=steps, lam=T * N / steps))
+    orders = [math.log(errs[0] / errs[1]) / math.log(1.5), math.log(errs[1] / errs[2]) / math.log(4 / 3)]
+    assert all(4.5 <= o <= 6.0 for o in orders), (errs, orders)
