@@ -236,84 +236,76 @@ __device__ __forceinline__ void transform_f32(float *x) {
       }
 }
 
-// FP32 hi + lo sums of packed pairs: (a.x + b.x, a.y + b.y) for two
-// independent values given as hi and lo pairs (Knuth's two-sum on packed
-// operands, then the lo parts added to the error)
-__device__ __forceinline__ void df_add_x2(float2 &ah, float2 &al, const float2 bh, const float2 bl) {
+// (ah, al) += sg * (bh, bl) for two independent values in packed lanes, in
+// FP32 hi + lo (Knuth's two-sum of the hi parts, the lo parts added to its
+// error); sg = +-1 (exact), so a - b costs the same as a + b.
+__device__ __forceinline__ void df_axpy_x2(float2 &ah, float2 &al, const float2 sg, const float2 bh, const float2 bl) {
   const float2 m1 = make_float2(-1.f, -1.f);
-  const float2 s = __fadd2_rn(ah, bh);
+  const float2 s = __ffma2_rn(sg, bh, ah);                 // fl(a + sg b)
   const float2 bb = __ffma2_rn(ah, m1, s);                 // s - a
   const float2 t1 = __ffma2_rn(bb, m1, s);                 // s - bb
   const float2 e1 = __ffma2_rn(t1, m1, ah);                // a - (s - bb)
-  const float2 e2 = __ffma2_rn(bb, m1, bh);                // b - bb
-  const float2 e = __fadd2_rn(__fadd2_rn(e1, e2), __fadd2_rn(al, bl));
+  const float2 e2 = __ffma2_rn(bb, m1, __fmul2_rn(sg, bh));  // sg b - bb
+  const float2 e = __fadd2_rn(__fadd2_rn(e1, e2), __ffma2_rn(sg, bl, al));
   ah = s;
   al = e;
 }
 
-// Corner transform restricted to one group of four output classes, in
-// FP32 hi + lo on packed pairs: the values z_q of corner data (xh, xl) with
-// ghost signs applied, for the four q whose top bit (3-D) belongs to group g
-// and input class p, out[j] = z_q with q & 3 = j.  3-D: the top
-// corner bit of q is fixed by the group; 2-D: the full 4-point transform.
+// Corner transform restricted to one group of four output classes, for two
+// inputs of the same input class at once (lane x: one input, lane y: the
+// next), in FP32 hi + lo: (zh[j], zl[j]) = z_q with q & 3 = j and the top
+// corner bit of q (3-D) fixed by group gi and input class p.
 template <int D>
-__device__ __forceinline__ void group_transform_x2(const float *xh, const float *xl, int gi, int p, float2 *out) {
-  float yh[4], yl[4];
-  if constexpr (D == 3) {
-    const float sg = ((gi ^ (p >> 2)) & 1) ? -1.0f : 1.0f;
-    float2 ah0 = make_float2(xh[0], xh[1]), al0 = make_float2(xl[0], xl[1]);
-    float2 ah1 = make_float2(xh[2], xh[3]), al1 = make_float2(xl[2], xl[3]);
-    df_add_x2(ah0, al0, make_float2(sg * xh[4], sg * xh[5]), make_float2(sg * xl[4], sg * xl[5]));
-    df_add_x2(ah1, al1, make_float2(sg * xh[6], sg * xh[7]), make_float2(sg * xl[6], sg * xl[7]));
-    yh[0] = ah0.x; yh[1] = ah0.y; yh[2] = ah1.x; yh[3] = ah1.y;
-    yl[0] = al0.x; yl[1] = al0.y; yl[2] = al1.x; yl[3] = al1.y;
-  } else {
+__device__ __forceinline__ void group_transform_pair(const float2 *h, const float2 *l, int gi, int p, float2 (&zh)[4],
+                                                     float2 (&zl)[4]) {
+  const float2 P1 = make_float2(1.f, 1.f), M1 = make_float2(-1.f, -1.f);
+  float2 yh[4], yl[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      yh[s] = xh[s];
-      yl[s] = xl[s];
-    }
+  for (int i = 0; i < 4; ++i) {
+    yh[i] = h[i];
+    yl[i] = l[i];
   }
-  // level over corner bit 0: (y0 + y1, y2 + y3) and (y0 - y1, y2 - y3)
-  float2 sh = make_float2(yh[0], yh[2]), sl = make_float2(yl[0], yl[2]);
-  float2 dh = sh, dl = sl;
-  df_add_x2(sh, sl, make_float2(yh[1], yh[3]), make_float2(yl[1], yl[3]));
-  df_add_x2(dh, dl, make_float2(-yh[1], -yh[3]), make_float2(-yl[1], -yl[3]));
-  // level over corner bit 1: q = 0: a0 + a2, 1: a1 + a3, 2: a0 - a2, 3: a1 - a3
-  float2 ph = make_float2(sh.x, dh.x), pl = make_float2(sl.x, dl.x);  // (a0, a1)
-  float2 mh = ph, ml = pl;
-  df_add_x2(ph, pl, make_float2(sh.y, dh.y), make_float2(sl.y, dl.y));    // (z0, z1)
-  df_add_x2(mh, ml, make_float2(-sh.y, -dh.y), make_float2(-sl.y, -dl.y));  // (z2, z3)
-  // in the order of the low two bits of q; class 4 g + cc takes q = cc ^ (p & 3)
-  out[0] = make_float2(ph.x, pl.x);
-  out[1] = make_float2(ph.y, pl.y);
-  out[2] = make_float2(mh.x, ml.x);
-  out[3] = make_float2(mh.y, ml.y);
+  if constexpr (D == 3) {
+    const float2 sg = ((gi ^ (p >> 2)) & 1) ? M1 : P1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) df_axpy_x2(yh[i], yl[i], sg, h[i + 4], l[i + 4]);
+  }
+  // corner bit 0: (y0 + y1, y0 - y1, y2 + y3, y2 - y3)
+  float2 ah[4] = {yh[0], yh[0], yh[2], yh[2]}, al[4] = {yl[0], yl[0], yl[2], yl[2]};
+  df_axpy_x2(ah[0], al[0], P1, yh[1], yl[1]);
+  df_axpy_x2(ah[1], al[1], M1, yh[1], yl[1]);
+  df_axpy_x2(ah[2], al[2], P1, yh[3], yl[3]);
+  df_axpy_x2(ah[3], al[3], M1, yh[3], yl[3]);
+  // corner bit 1: z0 = a0 + a2, z1 = a1 + a3, z2 = a0 - a2, z3 = a1 - a3
+  zh[0] = ah[0]; zl[0] = al[0];
+  zh[1] = ah[1]; zl[1] = al[1];
+  zh[2] = ah[0]; zl[2] = al[0];
+  zh[3] = ah[1]; zl[3] = al[1];
+  df_axpy_x2(zh[0], zl[0], P1, ah[2], al[2]);
+  df_axpy_x2(zh[1], zl[1], P1, ah[3], al[3]);
+  df_axpy_x2(zh[2], zl[2], M1, ah[2], al[2]);
+  df_axpy_x2(zh[3], zl[3], M1, ah[3], al[3]);
 }
 
-// Six signed 8-bit digits of two values at once (a packed pair: u = value of
-// one class, w = another), each v = (hi + lo) * sc with |v| <= 256:
-// v = sum_i d_i 2^(-8 i) up to a remainder below 2^-41.  Each digit is the
-// nearest integer to the rounded sum of the remainder pair (1.5 * 2^23 shift),
-// the remainder itself is kept exactly as hi and lo parts, so |d_0| <= 256 and
-// |d_i| <= 128 for i > 0 (every digit exact in BF16).
-__device__ __forceinline__ void six_digits2(float2 u, float2 w, float sc_u, float sc_w, float (&du)[kTcDigits],
-                                            float (&dw)[kTcDigits]) {
+// Six signed 8-bit digits of two values of one class at once (packed lanes),
+// each v = (hi + lo) * sc with |v| <= 256: v = sum_i d_i 2^(-8 i) up to a
+// remainder below 2^-41; d[i] holds digit i of both values.  Each digit is the
+// nearest integer to the rounded sum of the remainder pair (1.5 * 2^23
+// shift), the remainder itself is kept exactly as hi and lo parts, so
+// |d_0| <= 256 and |d_i| <= 128 for i > 0 (every digit exact in BF16).
+__device__ __forceinline__ void six_digits_pair(float2 h, float2 l, float2 sc, float2 (&d)[kTcDigits]) {
   const float2 C = make_float2(12582912.0f, 12582912.0f), S = make_float2(256.0f, 256.0f);
   const float2 M1 = make_float2(-1.0f, -1.0f);
-  float2 rh = make_float2(__fmul_rn(u.x, sc_u), __fmul_rn(w.x, sc_w));
-  float2 rl = make_float2(__fmul_rn(u.y, sc_u), __fmul_rn(w.y, sc_w));
+  float2 rh = __fmul2_rn(h, sc), rl = __fmul2_rn(l, sc);
 #pragma unroll
   for (int i = 0; i < kTcDigits; ++i) {
     if (i > 0) {
       rh = __fmul2_rn(rh, S);
       rl = __fmul2_rn(rl, S);
     }
-    // u - v is formed as fma(v, -1, u), which rounds like the subtraction
     const float2 q = __ffma2_rn(C, M1, __fadd2_rn(__fadd2_rn(rh, rl), C));
     rh = __ffma2_rn(q, M1, rh);
-    du[i] = q.x;
-    dw[i] = q.y;
+    d[i] = q;
   }
 }
 
@@ -488,58 +480,68 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
           squ[q] = cc == 0 ? scu[0] : cc == 1 ? scu[1] : cc == 2 ? scu[2] : scu[3];
           sqv[q] = cc == 0 ? scv[0] : cc == 1 ? scv[1] : cc == 2 ? scv[2] : scv[3];
         }
+        // two inputs per packed lane pair: positions (2j, 2j + 1) of this
+        // thread's eight; the corner data of pair j + 1 are loaded while pair j
+        // is transformed.  Positions past the class's inputs are zero padding
+        // (the same for the whole warp) and skip all arithmetic.
         uint32_t pk[kTcClasses][kTcDigits][4];
-        float dprev[kTcClasses][kTcDigits];
-        // corner data of input kk + 1 are loaded while input kk is transformed
-        float2 xn[NC];
-        auto load_corners = [&](int kk) {
-          const int b = s_inb[p * 16 + half * 8 + kk];
-          const float2 *plane = a.src + (size_t)max(b, 0) * g.ld_src;
-#pragma unroll
-          for (int s = 0; s < NC; ++s) xn[s] = (valid && b >= 0) ? plane[idx[s]] : make_float2(0.f, 0.f);
-        };
-        load_corners(0);
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          float xh[NC], xl[NC];
+        float2 nh[NC], nl[NC];
+        const int16_t *pin = s_inb + p * 16 + half * 8;
+        auto load_pair = [&](int j) {
+          const int b0 = pin[2 * j], b1 = pin[2 * j + 1];
+          if (b0 < 0) return;
+          const float2 *p0 = a.src + (size_t)b0 * g.ld_src;
+          const float2 *p1 = a.src + (size_t)(b1 >= 0 ? b1 : b0) * g.ld_src;
 #pragma unroll
           for (int s = 0; s < NC; ++s) {
-            xh[s] = xn[s].x;
-            xl[s] = xn[s].y;
+            const float2 v0 = p0[idx[s]], v1 = p1[idx[s]];
+            nh[s] = make_float2(v0.x, v1.x);
+            nl[s] = make_float2(v0.y, v1.y);
+          }
+        };
+        load_pair(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int b0 = pin[2 * j], b1 = pin[2 * j + 1];
+          if (b0 < 0) {
+#pragma unroll
+            for (int q = 0; q < kTcClasses; ++q)
+#pragma unroll
+              for (int i = 0; i < kTcDigits; ++i) pk[q][i][j] = 0u;
+            continue;
+          }
+          float2 xh[NC], xl[NC];
+#pragma unroll
+          for (int s = 0; s < NC; ++s) {
+            xh[s] = nh[s];
+            xl[s] = nl[s];
+          }
+          if (b1 < 0) {  // an odd class size: the second lane is padding
+#pragma unroll
+            for (int s = 0; s < NC; ++s) {
+              xh[s].y = 0.f;
+              xl[s].y = 0.f;
+            }
           }
           if (neg) {  // ghost images (non-periodic boundaries only)
 #pragma unroll
             for (int s = 0; s < NC; ++s)
               if ((neg >> s) & 1) {
-                xh[s] = -xh[s];
-                xl[s] = -xl[s];
+                xh[s] = make_float2(-xh[s].x, -xh[s].y);
+                xl[s] = make_float2(-xl[s].x, -xl[s].y);
               }
           }
-          if (kk < 7) load_corners(kk + 1);
-          float d[kTcClasses][kTcDigits];
-          // positions past the class's inputs are zero padding (the same for
-          // the whole warp): their digits are zero without any arithmetic
-          if (s_inb[p * 16 + half * 8 + kk] >= 0) {
-            float2 z[4];
-            group_transform_x2<D>(xh, xl, gi, p, z);
-            const bool isv = s_sh[p * 16 + half * 8 + kk] != 0;
-            six_digits2(z[0], z[1], isv ? sqv[0] : squ[0], isv ? sqv[1] : squ[1], d[0], d[1]);
-            six_digits2(z[2], z[3], isv ? sqv[2] : squ[2], isv ? sqv[3] : squ[3], d[2], d[3]);
-          } else {
+          if (j < 3) load_pair(j + 1);
+          float2 zh[4], zl[4];
+          group_transform_pair<D>(xh, xl, gi, p, zh, zl);
+          const bool v0 = s_sh[p * 16 + half * 8 + 2 * j] != 0, v1 = s_sh[p * 16 + half * 8 + 2 * j + 1] != 0;
 #pragma unroll
-            for (int cc = 0; cc < kTcClasses; ++cc)
+          for (int q = 0; q < kTcClasses; ++q) {
+            float2 d[kTcDigits];
+            six_digits_pair(zh[q], zl[q], make_float2(v0 ? sqv[q] : squ[q], v1 ? sqv[q] : squ[q]), d);
 #pragma unroll
-              for (int i = 0; i < kTcDigits; ++i) d[cc][i] = 0.f;
+            for (int i = 0; i < kTcDigits; ++i) pk[q][i][j] = pack_bf16x2(d[i].x, d[i].y);
           }
-#pragma unroll
-          for (int cc = 0; cc < kTcClasses; ++cc)
-#pragma unroll
-            for (int i = 0; i < kTcDigits; ++i) {
-              if (kk & 1)
-                pk[cc][i][kk >> 1] = pack_bf16x2(dprev[cc][i], d[cc][i]);
-              else
-                dprev[cc][i] = d[cc][i];
-            }
         }
         unsigned char *Ab = Abuf + buf * kTcBufA + tc::kmajor16_offset(node, half * 8);
 #pragma unroll
