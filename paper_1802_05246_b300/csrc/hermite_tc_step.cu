@@ -221,18 +221,18 @@ __device__ __forceinline__ float2 pow2_split(int e) {
   return make_float2(pow2f(e1), pow2f(e - e1));
 }
 
-// FP32 transform over all 2^d corners (butterflies in the order of the
-// corner bits): z[q] = sum_s (-1)^{|q & s|} x[s]
+// FP32 transform over all 2^d corners for two inputs at once (packed lanes;
+// butterflies in the order of the corner bits): z[q] = sum_s (-1)^{|q & s|} x[s]
 template <int D>
-__device__ __forceinline__ void transform_f32(float *x) {
+__device__ __forceinline__ void transform_f32_x2(float2 *x) {
 #pragma unroll
   for (int bm = 1; bm < (1 << D); bm <<= 1)
 #pragma unroll
     for (int i = 0; i < (1 << D); ++i)
       if (!(i & bm)) {
-        const float a = x[i], c = x[i | bm];
-        x[i] = __fadd_rn(a, c);
-        x[i | bm] = __fsub_rn(a, c);
+        const float2 a = x[i], c = x[i | bm];
+        x[i] = __fadd2_rn(a, c);
+        x[i | bm] = __ffma2_rn(c, make_float2(-1.f, -1.f), a);
       }
 }
 
@@ -401,31 +401,54 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
     }
     // ---- pre-pass: bound max |Y_c| for every output class (FP32 transform of
     // the hi parts; the lo parts and the roundings are covered by 2^-20 sum |x|)
+    // Two inputs per packed lane pair, the corners of the next pair loaded
+    // while this one is transformed.
     float mx[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) mx[c] = 0.f;
 #pragma unroll
     for (int p = 0; p < NC; ++p) {
       const uint32_t neg = (uint32_t)(negm >> (8 * p)) & 0xFF;
-      for (int kk = 0; kk < 8; ++kk) {
-        const int b = s_inb[p * 16 + half * 8 + kk];
-        if (b < 0) break;  // a class's inputs come first, the padding after
-        const float2 *plane = a.src + (size_t)b * g.ld_src;
-        float x[NC], S = 0.f;
+      const int16_t *pin = s_inb + p * 16 + half * 8;
+      float2 nx[NC];
+      auto load_pair = [&](int j) {
+        const int b0 = pin[2 * j], b1 = pin[2 * j + 1];
+        if (b0 < 0) return;
+        const float2 *p0 = a.src + (size_t)b0 * g.ld_src;
+        const float2 *p1 = a.src + (size_t)(b1 >= 0 ? b1 : b0) * g.ld_src;
+#pragma unroll
+        for (int s = 0; s < NC; ++s) nx[s] = make_float2(p0[idx[s]].x, p1[idx[s]].x);
+      };
+      load_pair(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int b0 = pin[2 * j], b1 = pin[2 * j + 1];
+        if (b0 < 0) break;  // a class's inputs come first, the padding after
+        float2 x[NC];
+#pragma unroll
+        for (int s = 0; s < NC; ++s) x[s] = nx[s];
+        if (b1 < 0) {
+#pragma unroll
+          for (int s = 0; s < NC; ++s) x[s].y = 0.f;
+        }
+        if (j < 3) load_pair(j + 1);
+        float2 S = make_float2(0.f, 0.f);
 #pragma unroll
         for (int s = 0; s < NC; ++s) {
-          x[s] = valid ? plane[idx[s]].x : 0.f;
-          S += fabsf(x[s]);
+          S.x += fabsf(x[s].x);
+          S.y += fabsf(x[s].y);
         }
         if (neg) {
 #pragma unroll
           for (int s = 0; s < NC; ++s)
-            if ((neg >> s) & 1) x[s] = -x[s];
+            if ((neg >> s) & 1) x[s] = make_float2(-x[s].x, -x[s].y);
         }
-        transform_f32<D>(x);
-        const float sc = pow2f(s_sh[p * 16 + half * 8 + kk]), slack = S * 9.5367431640625e-07f;
+        transform_f32_x2<D>(x);
+        const float2 sc = make_float2(pow2f(s_sh[p * 16 + half * 8 + 2 * j]), pow2f(s_sh[p * 16 + half * 8 + 2 * j + 1]));
+        const float2 sl = make_float2(S.x * 9.5367431640625e-07f * sc.x, S.y * 9.5367431640625e-07f * sc.y);
 #pragma unroll
-        for (int q = 0; q < NC; ++q) mx[q ^ p] = fmaxf(mx[q ^ p], (fabsf(x[q]) + slack) * sc);
+        for (int q = 0; q < NC; ++q)
+          mx[q ^ p] = fmaxf(mx[q ^ p], fmaxf(__fmaf_rn(fabsf(x[q].x), sc.x, sl.x), __fmaf_rn(fabsf(x[q].y), sc.y, sl.y)));
       }
     }
     // combine the two halves of each node's inputs
