@@ -34,6 +34,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint32_t
   return false;
 }
 
+// one arrival of this thread on the mbarrier (release: the thread's earlier
+// shared-memory writes are visible to whoever completes a wait on the phase)
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(b)) : "memory");
+}
+
 // the mbarrier expects `bytes` more transaction bytes and counts one arrival
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(b)), "r"(bytes) : "memory");

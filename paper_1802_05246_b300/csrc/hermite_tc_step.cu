@@ -341,8 +341,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
   int8_t *s_sh = s_er + kTcMaxNC * 16;                                 // [NC][16]
   uint64_t *bar = reinterpret_cast<uint64_t *>(s_sh + kTcMaxNC * 16);   // [2] MMAs of a buffer done
   uint64_t *bar_b = bar + 2;                                            // [2] operator chunk arrived
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 4);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  uint64_t *full = bar + 4;                                             // [2] every thread wrote its digits
+  uint64_t *tfree = bar + 6;                                            // every thread read the accumulators
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 7);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int node = tid & 127, half = tid >> 7;
   const Geometry &g = a.g;
   for (int i = tid; i < NC * 16; i += kTcThreads) {
@@ -358,6 +360,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
     tc::mbar_init(&bar[1], 1);
     tc::mbar_init(&bar_b[0], 1);
     tc::mbar_init(&bar_b[1], 1);
+    tc::mbar_init(&full[0], kTcThreads);
+    tc::mbar_init(&full[1], kTcThreads);
+    tc::mbar_init(tfree, kTcThreads);
     tc::mbar_fence_init();
   }
   if (warp == 0) {
@@ -369,11 +374,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
   tc::fence_after();
   const uint32_t tmem = *slot;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-  uint32_t it = 0;  // K chunks whose MMAs this CTA has issued
+  uint32_t it = 0;      // K chunks this CTA has produced
+  uint32_t groups = 0;  // class groups whose accumulators this CTA has read
+  // A wait that runs out marks this thread failed: from then on it skips its
+  // waits (so nothing waits on it for long) and the CTA stops at the next tile.
   bool failed = false;
-  bool tfail = false;  // thread 0: an operator-chunk wait ran out
+  auto wait = [&](uint64_t *b, uint32_t parity) {
+    if (!failed && !tc::mbar_wait(b, parity)) failed = true;
+  };
   const int64_t ntiles = (g.nodes_dst + 127) / 128;
-  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (__syncthreads_or(failed)) break;
     const int64_t t = tile * 128 + node;
     const bool valid = t < g.nodes_dst;
     int idx[NC];
@@ -470,7 +481,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
     for (int c = 0; c < NC; ++c) E[c] = bound_exponent(mxs[c * 128 + node]);
 #pragma unroll
     for (int gi = 0; gi < NG; ++gi) {
-      if (failed) break;
       // per-class digit scales of u and (balanced) v inputs
       float scu[kTcClasses], scv[kTcClasses];
 #pragma unroll
@@ -481,16 +491,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
       // ---- K loop over input parity classes
       for (int p = 0; p < NC; ++p, ++it) {
         const int buf = it & 1;
-        if (it >= 2) {
-          const bool ok = tc::mbar_wait(&bar[buf], ((it >> 1) - 1) & 1);
-          if (__syncthreads_or(!ok || tfail)) {
-            failed = true;
-            break;
-          }
-        }
+        // the chunk's MMAs are issued by one thread, warp it % 8 in turn, so
+        // the other warps go on with the next chunk meanwhile
+        const bool issuer = warp == (int)(it & 7) && lane == 0;
+        if (it >= 2) wait(&bar[buf], ((it >> 1) - 1) & 1);  // MMAs of chunk it - 2 done: buffers free
         // this chunk's operator digits arrive asynchronously while the
-        // threads produce the data digits; only the MMA issuer waits for them
-        if (tid == 0) {
+        // threads produce the data digits; only the issuer waits for them
+        if (issuer && !failed) {
           tc::mbar_expect_tx(&bar_b[buf], kTcBufB);
           tc::bulk_g2s(Bbuf + buf * kTcBufB, a.Bimg + (size_t)(gi * NC + p) * (kTcBufB / 16), kTcBufB, &bar_b[buf]);
         }
@@ -575,11 +582,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
             *reinterpret_cast<uint4 *>(Aq + i * kTcTileA) = make_uint4(pk[q][i][0], pk[q][i][1], pk[q][i][2], pk[q][i][3]);
         }
         tc::fence_async_smem();
-        __syncthreads();
-        // thread 0 waits for the operator chunk, then issues; a wait that runs
-        // out is reported at the next block barrier (the other threads go on)
-        if (tid == 0 && !tc::mbar_wait(&bar_b[buf], (it >> 1) & 1)) tfail = true;
-        if (tid == 0 && !tfail) {
+        tc::mbar_arrive(&full[buf]);
+        if (issuer) {
+          wait(&full[buf], (it >> 1) & 1);    // every thread's digits
+          wait(&bar_b[buf], (it >> 1) & 1);   // the operator digits
+          if (it >= 1) wait(&bar[(it - 1) & 1], ((it - 1) >> 1) & 1);  // chunk it - 1 first (another thread's MMAs)
+          if (p == 0 && groups > 0) wait(tfree, (groups - 1) & 1);     // accumulators read before they restart
+        }
+        if (issuer && !failed) {
           tc::fence_after();
           // digit-major order: consecutive MMAs go to different classes'
           // accumulators, which do not depend on one another
@@ -594,17 +604,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
             }
           tc::commit(&bar[buf]);
         }
+        __syncwarp();
       }
-      if (failed) break;
       // ---- epilogue: the seven diagonals of each class -> FP32 hi + lo outputs
-      {
-        const uint32_t last = it - 1;
-        const bool ok = !tfail && tc::mbar_wait(&bar[last & 1], (last >> 1) & 1);
-        if (__syncthreads_or(!ok)) {
-          failed = true;
-          break;
-        }
-      }
+      wait(&bar[(it - 1) & 1], ((it - 1) >> 1) & 1);  // the group's last MMAs (issued after all others)
       tc::fence_after();
 #pragma unroll
       for (int cq = 0; cq < 2; ++cq) {
@@ -630,13 +633,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         }
       }
       tc::fence_before();
-      __syncthreads();  // tensor memory read before the next group's first MMA overwrites it
+      tc::mbar_arrive(tfree);  // the next group's first MMA may overwrite the accumulators
+      ++groups;
     }
   }
-  if (failed) {
-    // let the MMAs still in flight finish (bounded) before the memory goes
-    if (it > 0) (void)tc::mbar_wait(&bar[(it - 1) & 1], ((it - 1) >> 1) & 1);
-    if (tid == 0) atomicExch(a.status, 1);
+  if (failed) atomicExch(a.status, 1);
+  // the last MMAs and operator copies (in flight only after a failure) end,
+  // bounded, before the tensor and shared memory go
+  if (it > 0) {
+    (void)tc::mbar_wait(&bar[(it - 1) & 1], ((it - 1) >> 1) & 1);
+    (void)tc::mbar_wait(&bar_b[(it - 1) & 1], ((it - 1) >> 1) & 1);
   }
   tc::fence_before();
   __syncthreads();
