@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
     }
     // ---- pre-pass: bound max |Y_c| for every output class (FP32 transform of
     // the hi parts; the lo parts and the roundings are covered by 2^-20 sum |x|)
-    // Two inputs per packed lane pair, the corners of the next pair loaded
-    // while this one is transformed.
+    // Two inputs per packed lane pair, the corners of the pair after next
+    // loaded while this one is transformed.
     float mx[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) mx[c] = 0.f;
@@ -421,28 +421,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
     for (int p = 0; p < NC; ++p) {
       const uint32_t neg = (uint32_t)(negm >> (8 * p)) & 0xFF;
       const int16_t *pin = s_inb + p * 16 + half * 8;
-      float2 nx[NC];
+      float2 nx[2][NC];
       auto load_pair = [&](int j) {
         const int b0 = pin[2 * j], b1 = pin[2 * j + 1];
         if (b0 < 0) return;
         const float2 *p0 = a.src + (size_t)b0 * g.ld_src;
         const float2 *p1 = a.src + (size_t)(b1 >= 0 ? b1 : b0) * g.ld_src;
 #pragma unroll
-        for (int s = 0; s < NC; ++s) nx[s] = make_float2(p0[idx[s]].x, p1[idx[s]].x);
+        for (int s = 0; s < NC; ++s) nx[j & 1][s] = make_float2(p0[idx[s]].x, p1[idx[s]].x);
       };
       load_pair(0);
+      load_pair(1);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int b0 = pin[2 * j], b1 = pin[2 * j + 1];
         if (b0 < 0) break;  // a class's inputs come first, the padding after
         float2 x[NC];
 #pragma unroll
-        for (int s = 0; s < NC; ++s) x[s] = nx[s];
+        for (int s = 0; s < NC; ++s) x[s] = nx[j & 1][s];
         if (b1 < 0) {
 #pragma unroll
           for (int s = 0; s < NC; ++s) x[s].y = 0.f;
         }
-        if (j < 3) load_pair(j + 1);
+        if (j < 2) load_pair(j + 2);
         float2 S = make_float2(0.f, 0.f);
 #pragma unroll
         for (int s = 0; s < NC; ++s) {
