@@ -480,14 +480,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
     int E[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) E[c] = bound_exponent(mxs[c * 128 + node]);
-#pragma unroll
+    // the group loop stays rolled: its body is large enough that two copies
+    // miss the instruction cache
+#pragma unroll 1
     for (int gi = 0; gi < NG; ++gi) {
+      // this group's four exponents (a select, not a run-time register index)
+      int Eg[kTcClasses];
+#pragma unroll
+      for (int cc = 0; cc < kTcClasses; ++cc) Eg[cc] = (NG > 1 && gi) ? E[(NG > 1 ? kTcClasses : 0) + cc] : E[cc];
       // per-class digit scales of u and (balanced) v inputs
       float scu[kTcClasses], scv[kTcClasses];
 #pragma unroll
       for (int cc = 0; cc < kTcClasses; ++cc) {
-        scu[cc] = pow2f(8 - E[gi * kTcClasses + cc]);
-        scv[cc] = pow2f(a.vexp + 8 - E[gi * kTcClasses + cc]);
+        scu[cc] = pow2f(8 - Eg[cc]);
+        scv[cc] = pow2f(a.vexp + 8 - Eg[cc]);
       }
       // ---- K loop over input parity classes
       for (int p = 0; p < NC; ++p, ++it) {
@@ -613,7 +619,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
 #pragma unroll
       for (int cq = 0; cq < 2; ++cq) {
         const int cc = half * 2 + cq, c = gi * kTcClasses + cc;
-        const int Ec = half ? E[gi * kTcClasses + 2 + cq] : E[gi * kTcClasses + cq];
+        const int Ec = half ? Eg[2 + cq] : Eg[cq];
         float acc[kTcMDigits][16];
 #pragma unroll
         for (int k = 0; k < kTcMDigits; ++k) tc::ld16(tmem + lane_base + cc * kTcCols + 16 * k, acc[k]);
