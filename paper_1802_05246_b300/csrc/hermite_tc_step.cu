@@ -417,10 +417,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
     float mx[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) mx[c] = 0.f;
-#pragma unroll
+    // the input-class loop stays rolled (code size): maxima are kept by q and
+    // moved to the classes c = q ^ p once per input class
+#pragma unroll 1
     for (int p = 0; p < NC; ++p) {
       const uint32_t neg = (uint32_t)(negm >> (8 * p)) & 0xFF;
       const int16_t *pin = s_inb + p * 16 + half * 8;
+      float tq[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) tq[q] = 0.f;
       float2 nx[2][NC];
       auto load_pair = [&](int j) {
         const int b0 = pin[2 * j], b1 = pin[2 * j + 1];
@@ -460,8 +465,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         const float2 sl = make_float2(S.x * 9.5367431640625e-07f * sc.x, S.y * 9.5367431640625e-07f * sc.y);
 #pragma unroll
         for (int q = 0; q < NC; ++q)
-          mx[q ^ p] = fmaxf(mx[q ^ p], fmaxf(__fmaf_rn(fabsf(x[q].x), sc.x, sl.x), __fmaf_rn(fabsf(x[q].y), sc.y, sl.y)));
+          tq[q] = fmaxf(tq[q], fmaxf(__fmaf_rn(fabsf(x[q].x), sc.x, sl.x), __fmaf_rn(fabsf(x[q].y), sc.y, sl.y)));
       }
+      // tq[q] -> class q ^ p: exchange the halves of every pair of entries
+      // that differ in a set bit of p
+#pragma unroll
+      for (int bm = 1; bm < NC; bm <<= 1)
+        if (p & bm)
+#pragma unroll
+          for (int q = 0; q < NC; ++q)
+            if (!(q & bm)) {
+              const float t0 = tq[q];
+              tq[q] = tq[q | bm];
+              tq[q | bm] = t0;
+            }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) mx[c] = fmaxf(mx[c], tq[c]);
     }
     // combine the two halves of each node's inputs
     if (half) {
@@ -616,10 +635,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
       // ---- epilogue: the seven diagonals of each class -> FP32 hi + lo outputs
       wait(&bar[(it - 1) & 1], ((it - 1) >> 1) & 1);  // the group's last MMAs (issued after all others)
       tc::fence_after();
-#pragma unroll
+#pragma unroll 1
       for (int cq = 0; cq < 2; ++cq) {
         const int cc = half * 2 + cq, c = gi * kTcClasses + cc;
-        const int Ec = half ? Eg[2 + cq] : Eg[cq];
+        const int Ec = half ? (cq ? Eg[3] : Eg[2]) : (cq ? Eg[1] : Eg[0]);
         float acc[kTcMDigits][16];
 #pragma unroll
         for (int k = 0; k < kTcMDigits; ++k) tc::ld16(tmem + lane_base + cc * kTcCols + 16 * k, acc[k]);
