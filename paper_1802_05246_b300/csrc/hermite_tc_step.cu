@@ -294,18 +294,20 @@ __device__ __forceinline__ void group_transform_pair(const float2 *h, const floa
 // shift), the remainder itself is kept exactly as hi and lo parts, so
 // |d_0| <= 256 and |d_i| <= 128 for i > 0 (every digit exact in BF16).
 __device__ __forceinline__ void six_digits_pair(float2 h, float2 l, float2 sc, float2 (&d)[kTcDigits]) {
-  const float2 C = make_float2(12582912.0f, 12582912.0f), S = make_float2(256.0f, 256.0f);
+  // digit i is taken at granularity 2^(-8 i) (shift constant 1.5 * 2^(23 - 8 i))
+  // and only the digit is scaled back to an integer: the same roundings as
+  // scaling the remainder by 256 before every digit, one multiply fewer
   const float2 M1 = make_float2(-1.0f, -1.0f);
   float2 rh = __fmul2_rn(h, sc), rl = __fmul2_rn(l, sc);
+  float ci = 12582912.0f, si = 1.0f;  // 1.5 * 2^(23 - 8 i) and 2^(8 i), exact
 #pragma unroll
   for (int i = 0; i < kTcDigits; ++i) {
-    if (i > 0) {
-      rh = __fmul2_rn(rh, S);
-      rl = __fmul2_rn(rl, S);
-    }
-    const float2 q = __ffma2_rn(C, M1, __fadd2_rn(__fadd2_rn(rh, rl), C));
+    const float2 C = make_float2(ci, ci);
+    const float2 q = __ffma2_rn(C, M1, __fadd2_rn(__fadd2_rn(rh, rl), C));  // a multiple of 2^(-8 i)
     rh = __ffma2_rn(q, M1, rh);
-    d[i] = q;
+    d[i] = i == 0 ? q : __fmul2_rn(q, make_float2(si, si));
+    ci *= 0.00390625f;
+    si *= 256.0f;
   }
 }
 
