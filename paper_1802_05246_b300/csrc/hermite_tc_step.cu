@@ -180,9 +180,15 @@ extern "C" int hermite_tc_selftest(int K, int N, float *A, float *B, float *D0, 
 // tensor memory.  Per input parity class p (a 16-wide K chunk, whose inputs
 // share their parity and so their ghost signs), the threads write the digits
 // of their inputs to one of two shared-memory A buffers while the tensor core
-// works on the other; thread 0 issues 24 MMAs (4 classes x 6 data digits,
-// N = 16 (7 - i) operator digits each) and commits them to the buffer's
-// mbarrier; the epilogue reads the diagonals with tcgen05.ld.
+// works on the other; each thread handles two inputs per packed FP32 lane
+// pair (transform, digits and BF16x2 packing without lane shuffles).  Every
+// thread arrives on the buffer's mbarrier when its digits are stored; lane 0
+// of warp (chunk % 8) waits for all of them, for the operator chunk (a bulk
+// copy it started) and for the previous chunk's MMAs, then issues 24 MMAs
+// (4 classes x 6 data digits, N = 16 (7 - i) operator digits each) and
+// commits them to the buffer's mbarrier, which frees the buffer two chunks
+// later.  The epilogue reads the diagonals with tcgen05.ld and arrives on a
+// barrier that the next group's first MMA waits for.  Every wait is bounded.
 // ---------------------------------------------------------------------------
 namespace hermite {
 namespace {
