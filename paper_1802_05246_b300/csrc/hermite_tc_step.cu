@@ -173,7 +173,8 @@ extern "C" int hermite_tc_selftest(int K, int N, float *A, float *B, float *D0, 
 //
 // Work split: a CTA owns 128 consecutive target nodes at a time (one per
 // tensor-memory lane); 256 threads, thread t and t + 128 share a node and
-// take the first and the second 8 inputs of each 16-input parity class.
+// take K slots 0-7 and 8-15 of each 16-wide parity-class chunk (a class's
+// inputs are dealt to the two halves in pairs, in turn: see k_slot).
 // Per tile, one FP32 pre-pass over the corner data bounds max |Y_c| for all
 // classes.  Output classes then go in groups of four (3-D: two groups), so
 // that a group's accumulators (4 classes x 7 diagonals x 16 columns) fit in
@@ -695,6 +696,18 @@ namespace hermite {
 // (group, input class p, class cc of the group) holds rows j * 16 + n (digit
 // j of output n of class 4 group + cc) and K columns k (input k of class p),
 // zero where a class has fewer than 16 members.
+namespace {
+// K slot of the k-th input of a parity class: consecutive input pairs go to
+// the two halves of the 16 slots in turn (slots 0-7 are read by the first
+// thread of each node, 8-15 by the second), so that both threads of a node
+// get about half of a class's 9-16 inputs; each half keeps its real inputs
+// first and its padding after.
+int k_slot(int k) {
+  const int pair = k >> 1;
+  return (pair & 1) * 8 + (pair >> 1) * 2 + (k & 1);
+}
+}  // namespace
+
 int build_tc_operator(hermite_ctx *ctx) {
   ctx->tc_ready = false;
   ctx->split_engine = 0;
@@ -747,13 +760,13 @@ int build_tc_operator(hermite_ctx *ctx) {
               const float f = (float)dg;  // an integer of at most 9 bits: its BF16 is the top half
               uint32_t bits;
               std::memcpy(&bits, &f, 4);
-              tile[tc::kmajor16_offset(j * 16 + (int)n, (int)k) / 2] = (uint16_t)(bits >> 16);
+              tile[tc::kmajor16_offset(j * 16 + (int)n, k_slot((int)k)) / 2] = (uint16_t)(bits >> 16);
             }
           }
       }
   std::vector<int16_t> inb((size_t)NC * 16, -1), orow((size_t)NC * 16, -1);
   for (int c = 0; c < NC; ++c) {
-    for (size_t k = 0; k < in_cls[c].size(); ++k) inb[c * 16 + k] = (int16_t)in_cls[c][k];
+    for (size_t k = 0; k < in_cls[c].size(); ++k) inb[c * 16 + k_slot((int)k)] = (int16_t)in_cls[c][k];
     for (size_t n = 0; n < out_cls[c].size(); ++n) orow[c * 16 + n] = (int16_t)out_cls[c][n];
   }
   if (!cuda_ok(ctx, device_alloc(&ctx->tc_B, img.size() * 2), "cudaMalloc tc_B") ||
