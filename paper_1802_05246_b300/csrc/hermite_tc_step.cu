@@ -549,9 +549,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         // thread's eight; the corner data of pair j + 1 are loaded while pair j
         // is transformed.  Positions past the class's inputs are zero padding
         // (the same for the whole warp) and skip all arithmetic.
-        uint32_t pk[kTcClasses][kTcDigits][4];
+        uint32_t pk[kTcClasses][kTcDigits][2];  // two pairs of digits: one 8-byte word per class and digit
         float2 nh[NC], nl[NC];
         const int16_t *pin = s_inb + p * 16 + half * 8;
+        unsigned char *Ab = Abuf + buf * kTcBufA + tc::kmajor16_offset(node, half * 8);
         auto load_pair = [&](int j) {
           const int b0 = pin[2 * j], b1 = pin[2 * j + 1];
           if (b0 < 0) return;
@@ -572,49 +573,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
 #pragma unroll
             for (int q = 0; q < kTcClasses; ++q)
 #pragma unroll
-              for (int i = 0; i < kTcDigits; ++i) pk[q][i][j] = 0u;
-            continue;
-          }
-          float2 xh[NC], xl[NC];
-#pragma unroll
-          for (int s = 0; s < NC; ++s) {
-            xh[s] = nh[s];
-            xl[s] = nl[s];
-          }
-          if (b1 < 0) {  // an odd class size: the second lane is padding
+              for (int i = 0; i < kTcDigits; ++i) pk[q][i][j & 1] = 0u;
+          } else {
+            float2 xh[NC], xl[NC];
 #pragma unroll
             for (int s = 0; s < NC; ++s) {
-              xh[s].y = 0.f;
-              xl[s].y = 0.f;
+              xh[s] = nh[s];
+              xl[s] = nl[s];
+            }
+            if (b1 < 0) {  // an odd class size: the second lane is padding
+#pragma unroll
+              for (int s = 0; s < NC; ++s) {
+                xh[s].y = 0.f;
+                xl[s].y = 0.f;
+              }
+            }
+            if (neg) {  // ghost images (non-periodic boundaries only)
+#pragma unroll
+              for (int s = 0; s < NC; ++s)
+                if ((neg >> s) & 1) {
+                  xh[s] = make_float2(-xh[s].x, -xh[s].y);
+                  xl[s] = make_float2(-xl[s].x, -xl[s].y);
+                }
+            }
+            if (j < 3) load_pair(j + 1);
+            float2 zh[4], zl[4];
+            group_transform_pair<D>(xh, xl, gi, p, zh, zl);
+            const bool v0 = s_sh[p * 16 + half * 8 + 2 * j] != 0, v1 = s_sh[p * 16 + half * 8 + 2 * j + 1] != 0;
+#pragma unroll
+            for (int q = 0; q < kTcClasses; ++q) {
+              float2 d[kTcDigits];
+              six_digits_pair(zh[q], zl[q], make_float2(v0 ? sqv[q] : squ[q], v1 ? sqv[q] : squ[q]), d);
+#pragma unroll
+              for (int i = 0; i < kTcDigits; ++i) pk[q][i][j & 1] = pack_bf16x2(d[i].x, d[i].y);
             }
           }
-          if (neg) {  // ghost images (non-periodic boundaries only)
+          if (j & 1) {  // positions 4 (j >> 1) .. + 3 of this thread's eight
 #pragma unroll
-            for (int s = 0; s < NC; ++s)
-              if ((neg >> s) & 1) {
-                xh[s] = make_float2(-xh[s].x, -xh[s].y);
-                xl[s] = make_float2(-xl[s].x, -xl[s].y);
-              }
+            for (int q = 0; q < kTcClasses; ++q) {
+              unsigned char *Aq = Ab + (q ^ (p & 3)) * kTcDigits * kTcTileA + 8 * (j >> 1);
+#pragma unroll
+              for (int i = 0; i < kTcDigits; ++i)
+                *reinterpret_cast<uint2 *>(Aq + i * kTcTileA) = make_uint2(pk[q][i][0], pk[q][i][1]);
+            }
           }
-          if (j < 3) load_pair(j + 1);
-          float2 zh[4], zl[4];
-          group_transform_pair<D>(xh, xl, gi, p, zh, zl);
-          const bool v0 = s_sh[p * 16 + half * 8 + 2 * j] != 0, v1 = s_sh[p * 16 + half * 8 + 2 * j + 1] != 0;
-#pragma unroll
-          for (int q = 0; q < kTcClasses; ++q) {
-            float2 d[kTcDigits];
-            six_digits_pair(zh[q], zl[q], make_float2(v0 ? sqv[q] : squ[q], v1 ? sqv[q] : squ[q]), d);
-#pragma unroll
-            for (int i = 0; i < kTcDigits; ++i) pk[q][i][j] = pack_bf16x2(d[i].x, d[i].y);
-          }
-        }
-        unsigned char *Ab = Abuf + buf * kTcBufA + tc::kmajor16_offset(node, half * 8);
-#pragma unroll
-        for (int q = 0; q < kTcClasses; ++q) {
-          unsigned char *Aq = Ab + (q ^ (p & 3)) * kTcDigits * kTcTileA;
-#pragma unroll
-          for (int i = 0; i < kTcDigits; ++i)
-            *reinterpret_cast<uint4 *>(Aq + i * kTcTileA) = make_uint4(pk[q][i][0], pk[q][i][1], pk[q][i][2], pk[q][i][3]);
         }
         tc::fence_async_smem();
         tc::mbar_arrive(&full[buf]);
