@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
   tc::fence_after();
   const uint32_t tmem = *slot;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const uint64_t desc_a0 = tc::desc_kmajor(Abuf, 128, 256), desc_b0 = tc::desc_kmajor(Bbuf, 128, 256);
   uint32_t it = 0;      // K chunks this CTA has produced
   uint32_t groups = 0;  // class groups whose accumulators this CTA has read
   // A wait that runs out marks this thread failed: from then on it skips its
@@ -629,16 +630,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) half_step_tc_kernel(const TcArg
         if (issuer && !failed) {
           tc::fence_after();
           // digit-major order: consecutive MMAs go to different classes'
-          // accumulators, which do not depend on one another
+          // accumulators, which do not depend on one another.  Descriptors are
+          // the buffer's base descriptor plus the tile offset in 16-byte units
+          // (shared-memory addresses stay below 2^18, inside the 14-bit field).
+          const uint64_t da0 = desc_a0 + (uint64_t)((buf * kTcBufA) >> 4);
+          const uint64_t db0 = desc_b0 + (uint64_t)((buf * kTcBufB) >> 4);
 #pragma unroll
           for (int i = 0; i < kTcDigits; ++i)
 #pragma unroll
-            for (int cc = 0; cc < kTcClasses; ++cc) {
-              const uint64_t db = tc::desc_kmajor(Bbuf + buf * kTcBufB + cc * kTcTileB, 128, 256);
-              const uint64_t da = tc::desc_kmajor(Abuf + buf * kTcBufA + (cc * kTcDigits + i) * kTcTileA, 128, 256);
-              tc::mma(tmem + cc * kTcCols + 16 * i, da, db, tc::idesc_bf16(128, 16 * (kTcMDigits - i)),
+            for (int cc = 0; cc < kTcClasses; ++cc)
+              tc::mma(tmem + cc * kTcCols + 16 * i, da0 + (uint64_t)(((cc * kTcDigits + i) * kTcTileA) >> 4),
+                      db0 + (uint64_t)((cc * kTcTileB) >> 4), tc::idesc_bf16(128, 16 * (kTcMDigits - i)),
                       (p > 0 || i > 0) ? 1u : 0u);
-            }
           tc::commit(&bar[buf]);
         }
         __syncwarp();
