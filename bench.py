@@ -74,6 +74,7 @@ ALG_BYTES_PER_LAUNCH = 2 * DOF_PER_HALF * 8
 # 64^3, scaled to 128^3 by the node count
 TRAFFIC_PER_LAUNCH = 373.8e6 * 8
 SPLIT_TRAFFIC_PER_LAUNCH = 362.3e6 * 8
+TC_TRAFFIC_PER_LAUNCH = 350.2e6 * 8
 # tensor-core flops of the digit-split engine per node: 8 output classes x 8
 # input classes (K = 16 each) x sum over the six data digits i of N = 16 (7 - i)
 # operator-digit columns, two flops per multiply-add
@@ -501,7 +502,8 @@ def run_ours(args):
                      "engine": "tensor cores (tcgen05): six BF16 data digits x seven operator digits, exact FP32 "
                                "accumulation (hermite_set_split_engine 1)",
                      "l2_err": errtc, "ratio_over_fp64": None if err64 is None else errtc / err64,
-                     "roofline": roofline("half_step_tc_kernel<3>", tcm["half_ms"], None, "tensor (BF16 digits)",
+                     "roofline": roofline("half_step_tc_kernel<3>", tcm["half_ms"], TC_TRAFFIC_PER_LAUNCH,
+                                          "tensor (BF16 digits)",
                                           pk.get("bf16_tflops"), NODES * TC_FLOP_PER_NODE)},
         "fp64": {"value": value64, "ms_per_step": fp64["ms"] / args.steps, "dtype": "f64",
                  "roofline": roofline("half_step_f64_kernel<3,92>", fp64["half_ms"], TRAFFIC_PER_LAUNCH, "FP64",
